@@ -22,8 +22,8 @@
  *   - grid coordinate x = N/2 + u*FoV (cells), tap start i0 = ceil(x - W/2),
  *     W consecutive cells i0..i0+W-1 weighted by G(i - x);
  *   - a visibility whose footprint leaves [0,N) on either axis is dropped;
- *   - planes are cell-centred: k = clamp(floor((w - w_min)/dw), 0, N_w-1),
- *     dw = (w_max - w_min)/N_w, plane centre w_k = w_min + (k + 1/2) dw;
+ *   - planes are cell-centred: k = clamp(floor((w - w_min) * (N_w/(w_max - w_min))),
+ *     0, N_w-1), plane centre w_k = w_min + (k + 1/2) dw, dw = (w_max - w_min)/N_w;
  *   - image pixel (a, b) sits at l = (a - N/2) FoV/N, m = (b - N/2) FoV/N,
  *     stored row-major with row index b (m) and column index a (l);
  *   - the output is the unnormalised dirty image
@@ -165,10 +165,12 @@ static int locate_one(const wo_config *c, float uf, float vf, float wf, int32_t 
   const double ci = ceil(xx - half_w);
   const double cj = ceil(yy - half_w);
   if (ci < 0.0 || cj < 0.0 || ci + c->support > c->n || cj + c->support > c->n) return WO_DROPPED;
-  const double dw = plane_width(c);
+  /* plane scale N_w / (w_max - w_min): one rounded product per visibility */
+  const double range = c->w_max - c->w_min;
   int32_t kk = 0;
-  if (dw > 0.0) {
-    const double q = floor(((double)wf - c->w_min) / dw);
+  if (range > 0.0) {
+    const double scale = (double)c->n_w / range;
+    const double q = floor(((double)wf - c->w_min) * scale);
     if (q < 0.0)
       kk = 0;
     else if (q > c->n_w - 1)
