@@ -1,0 +1,241 @@
+/*
+ * wst.h -- C ABI of libwst, a GB300 (sm_103a) w-stacking imager.
+ *
+ * Method: Gheller, Taffoni & Goz, "High Performance W-stacking for Imaging Radio
+ * Astronomy Data: a Parallel and Accelerated Solution", arXiv:2301.06061.
+ *   section 2, Eq. 1   measurement equation (what a visibility is)
+ *   section 2, Eq. 2   w-stacking inversion: per w-plane 2D Fourier transform,
+ *                      phase correction exp(2 pi i w (n - 1)), sum over planes
+ *   section 2, Eq. 3   convolutional gridding with a Gaussian kernel of 7 cells
+ *   section 2 / 3.2    pipeline: gridding -> FFT per w-plane -> phase shift and
+ *                      reduction of the w-planes into the final image
+ *
+ * Conventions used by every entry point
+ *   - N x N image, N a power of two in [64, 16384]; field of view FoV radians;
+ *     pixel (a, b) sits at l = (a - N/2) FoV/N, m = (b - N/2) FoV/N; images are
+ *     complex64 (interleaved re, im), row-major with row index b (m axis).
+ *   - Grid cell (p, q) holds u = (p - N/2)/FoV, v = (q - N/2)/FoV wavelengths;
+ *     planes are complex64, row-major with row index q (v axis).
+ *   - A visibility at x = N/2 + u FoV (computed in FP64) touches the W cells
+ *     i0 = ceil(x - W/2) ... i0 + W - 1 with weight G(i - x) (same along v).
+ *     A visibility whose footprint leaves [0, N) on either axis is dropped and
+ *     counted; one with a non-finite u, v, w, value or weight is counted apart.
+ *   - Planes are cell-centred on [w_min, w_max]: k = clamp(floor((w - w_min) *
+ *     (N_w / (w_max - w_min))), 0, N_w - 1), centre w_k = w_min + (k + 1/2) dw.
+ *   - The image is the unnormalised dirty image
+ *       D(a,b) = sum_k e^{+2 pi i w_k (n-1)} F_k(a,b) / (Ghat(nu_a) Ghat(nu_b)),
+ *     F_k the centred 2D transform of plane k with the positive exponent,
+ *     n - 1 = -(l^2+m^2)/(1+sqrt(1-l^2-m^2)), nu_a = (a - N/2)/N, Ghat the
+ *     Fourier transform of the truncated kernel; D = 0 where l^2 + m^2 >= 1.
+ *
+ * Memory and errors
+ *   - Every data pointer is a DEVICE pointer owned by the caller unless stated;
+ *     it is borrowed for the duration of the stream work the call enqueues.
+ *   - All work is enqueued on the plan's CUDA stream; calls return once it is
+ *     enqueued.  Argument errors are reported synchronously.  Device-side
+ *     conditions (e.g. a bounded wait running out) set a device error word that
+ *     wst_get_stats reads (it synchronises the stream).
+ *   - No entry point traps, aborts or exits; nothing throws across the ABI.
+ *   - Scratch memory ("workspace") is caller-provided device memory
+ *     (wst_plan_workspace_bytes / wst_plan_set_workspace).  The plan itself owns
+ *     only small tables (twiddles, grid-correction, screen terms) it allocates
+ *     with cudaMalloc at creation.
+ */
+#ifndef WST_H
+#define WST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum wst_status {
+  WST_OK = 0,
+  WST_ERR_INVALID_ARG = 1, /* a pointer, size or configuration value is invalid   */
+  WST_ERR_OOM = 2,         /* a table allocation failed or the workspace is short  */
+  WST_ERR_CUDA = 3,        /* a CUDA runtime call failed (see wst_last_error)      */
+  WST_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out                   */
+  WST_ERR_UNSUPPORTED = 5, /* valid but outside what this build implements         */
+  WST_ERR_STATE = 6        /* call out of order (e.g. no visibilities set)         */
+} wst_status;
+
+/* Convolution kernels G (section 2, Eq. 3). */
+enum {
+  WST_KERNEL_GAUSS = 0, /* exp(-x^2 / (2 sigma^2)), |x| <= W/2; kparam = sigma (cells) */
+  WST_KERNEL_ES = 1,    /* exp(beta (sqrt(1 - (2x/W)^2) - 1));  kparam = beta        */
+  WST_KERNEL_TABLE = 2  /* piecewise-linear samples on [-W/2, W/2], ktable_len of them */
+};
+
+/* wst_config.flags */
+#define WST_FLAG_KAHAN 0x1u       /* compensated (Kahan) accumulation of the planes   */
+#define WST_FLAG_FP64_SCREEN 0x2u /* phase argument in native FP64, not float-float   */
+#define WST_FLAG_TIMING 0x4u      /* record per-stage CUDA-event times in wst_image   */
+
+/* per-call flags of wst_image / wst_correct / wst_degrid / wst_kernel_grad */
+#define WST_NO_CORRECTION 0x1u /* omit the 1/(Ghat(nu_a) Ghat(nu_b)) grid correction */
+
+typedef struct wst_config {
+  int32_t n;                /* image side N, power of two, 64..16384                  */
+  double fov;               /* field of view in radians (> 0)                          */
+  int32_t n_w;              /* w-planes per image, 1..4096                             */
+  double w_min, w_max;      /* plane range (wavelengths); equal => min/max of the data */
+  int32_t support;          /* kernel support W in cells, 2..16                        */
+  int32_t kernel;           /* WST_KERNEL_*                                            */
+  double kparam;            /* sigma (GAUSS) or beta (ES); unused for TABLE            */
+  int32_t ktable_len;       /* TABLE: number of samples, 2..65536                      */
+  uint32_t flags;           /* WST_FLAG_*                                              */
+  int32_t planes_per_chunk; /* planes held in the workspace at once; 0 = all           */
+  int32_t batch;            /* independent images sharing this geometry, >= 1          */
+} wst_config;
+
+typedef struct wst_stats {
+  int64_t n_vis;       /* visibilities passed to wst_plan_set_vis                      */
+  int64_t n_kept;      /* visibilities gridded                                         */
+  int64_t n_dropped;   /* footprint outside the grid                                   */
+  int64_t n_nonfinite; /* non-finite u, v, w, value or weight                          */
+  double w_min, w_max; /* plane range of image 0                                       */
+  float ms_sort, ms_grid, ms_fft, ms_correct, ms_total; /* last wst_image (TIMING flag) */
+  int32_t device_error; /* 0, or a WST_ERR_* raised on the device                       */
+  int32_t n_chunks;     /* plane chunks used by wst_image                               */
+} wst_stats;
+
+typedef struct wst_plan_s *wst_plan;
+
+/* Library version string, e.g. "0.1.0". */
+const char *wst_version(void);
+
+/* Static description of a status code. */
+const char *wst_status_string(wst_status s);
+
+/*
+ * Create a plan for one imaging geometry (section 2: the mesh N_u x N_v x N_w and
+ * the kernel of Eq. 3).  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Builds, on the device, the FFT twiddles, the grid-correction table
+ * 1/Ghat(nu) (Gauss-Legendre quadrature in FP64) and the l^2 terms of the phase
+ * screen.  For WST_KERNEL_TABLE the correction is built by wst_plan_set_kernel_table.
+ * Errors: INVALID_ARG (bad config), UNSUPPORTED, OOM, CUDA.  *out is NULL on error.
+ */
+wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *out);
+
+/* Release the plan's tables.  Waits for the plan's stream. NULL is a no-op. */
+void wst_plan_destroy(wst_plan plan);
+
+/* Change the stream subsequent calls enqueue on. */
+wst_status wst_plan_set_stream(wst_plan plan, void *cuda_stream);
+
+/*
+ * Bytes of device workspace needed for `n_vis` visibilities (sort buffers,
+ * bucket offsets, one chunk of planes, compensation image).  Host-only call.
+ */
+wst_status wst_plan_workspace_bytes(wst_plan plan, int64_t n_vis, size_t *bytes);
+
+/*
+ * Hand the plan a caller-owned device buffer of `bytes` bytes (256-byte aligned).
+ * It must stay valid while the plan uses it.  Errors: INVALID_ARG (NULL, misaligned).
+ */
+wst_status wst_plan_set_workspace(wst_plan plan, void *device_ptr, size_t bytes);
+
+/*
+ * WST_KERNEL_TABLE only: copy `ktable_len` FP32 samples (device pointer) of G on
+ * [-W/2, W/2] into the plan and rebuild 1/Ghat on the device (the integral of a
+ * piecewise-linear function times cos, in closed form per interval, FP64).
+ */
+wst_status wst_plan_set_kernel_table(wst_plan plan, const float *table_dev);
+
+/*
+ * Bind visibilities and bucket-sort them (device) by (image, plane, 64x64 tile).
+ * u, v, w: FP32 [n_vis] wavelengths; vis: complex64 [n_vis]; weight: FP32 [n_vis]
+ * or NULL (natural weights 1).  batch_offsets: HOST int64 [batch + 1], image i
+ * owns visibilities [off[i], off[i+1]) (NULL allowed when batch == 1).  The
+ * plane range is taken from the config or, if w_min == w_max, from the min/max
+ * of the finite w of each image.  The inputs are read during this call's stream
+ * work only (values are copied into the sorted records).  Errors: INVALID_ARG,
+ * OOM (workspace missing or too small), CUDA.
+ */
+wst_status wst_plan_set_vis(wst_plan plan, int64_t n_vis, const float *u, const float *v,
+                            const float *w, const void *vis, const float *weight,
+                            const int64_t *batch_offsets);
+
+/*
+ * Eq. 3: grid planes [plane_begin, plane_end) (global plane index image*N_w + k)
+ * into grid_out, complex64 [(plane_end - plane_begin) x N x N], natural layout.
+ */
+wst_status wst_grid(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *grid_out);
+
+/*
+ * Eq. 2 for planes [plane_begin, plane_end): transform each plane of grid_inout
+ * (layout of wst_grid; overwritten) with the centred positive-exponent 2D FFT,
+ * multiply by the plane's phase screen and ADD into image_inout, complex64
+ * [batch x N x N].  No grid correction (see wst_correct).
+ */
+wst_status wst_fft_correct(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *grid_inout,
+                           void *image_inout);
+
+/* Multiply image_inout [batch x N x N] by 1/(Ghat(nu_a) Ghat(nu_b)). */
+wst_status wst_correct(wst_plan plan, void *image_inout);
+
+/*
+ * The whole hot path (Eq. 2-3): grid, FFT, phase screen and plane sum for every
+ * plane of every image, then the grid correction (unless WST_NO_CORRECTION).
+ * image_out: complex64 [batch x N x N], overwritten.  Planes are processed in
+ * chunks of planes_per_chunk held in the workspace; with WST_FLAG_KAHAN the
+ * plane sum is compensated on chip within a chunk and across chunks.
+ */
+wst_status wst_image(wst_plan plan, void *image_out, uint32_t flags);
+
+/*
+ * Adjoint of wst_image (degridding; the paper lists it as future work in its
+ * conclusions): dvis_j = w_j sum_taps G G g_k[q,p], g_k the centred 2D transform
+ * with the negative exponent of conj(screen_k) * C_a C_b * dimage.
+ * dimage: complex64 [batch x N x N]; dvis_out: complex64 [n_vis] in the caller's
+ * order (0 for dropped and non-finite visibilities).
+ */
+wst_status wst_degrid(wst_plan plan, const void *dimage, void *dvis_out, uint32_t flags);
+
+/*
+ * WST_KERNEL_TABLE only: gradient of Re<dimage, U> with respect to the kernel
+ * samples, U the image without grid correction (WST_NO_CORRECTION must be set:
+ * the correction's dependence on the table is left to the caller).
+ * dtable_out: FP32 [ktable_len], overwritten.
+ */
+wst_status wst_kernel_grad(wst_plan plan, const void *dimage, float *dtable_out, uint32_t flags);
+
+/*
+ * Per visibility, in the caller's order, the plane k (within its image) and
+ * tap starts i0 (u axis) and j0 (v axis) assigned by the sort, or -1 for a
+ * dropped or non-finite one.  int32 device arrays [n_vis].
+ */
+wst_status wst_vis_cells(wst_plan plan, int32_t *plane_out, int32_t *i0_out, int32_t *j0_out);
+
+/* Counters, plane range and timings.  Synchronises the plan's stream. */
+wst_status wst_get_stats(wst_plan plan, wst_stats *out);
+
+/* Message of the last error on this plan ("" if none).  Valid until the next call. */
+const char *wst_last_error(wst_plan plan);
+
+/*
+ * Direct transform (the exact dirty image; conjugate of Eq. 1) at n_pix pixels:
+ *   out_i = sum_j w_j V_j exp(2 pi i (u_j l + v_j m + w_j (n - 1))),
+ * l, m from (pa_i, pb_i) on an N x N grid of spacing fov/N.  Phase arguments are
+ * formed and reduced modulo one cycle in float-float (about 44 bits), the sum in
+ * FP32 with per-block partial sums.  pa, pb: int32 device [n_pix]; out: complex64.
+ */
+wst_status wst_dft(int64_t n_vis, const float *u, const float *v, const float *w, const void *vis,
+                   const float *weight, int32_t n, double fov, int64_t n_pix, const int32_t *pa,
+                   const int32_t *pb, void *out, void *cuda_stream);
+
+/*
+ * Eq. 1 for a point-source sky: V_j = sum_s S_s exp(-2 pi i (u_j l_s + v_j m_s +
+ * w_j (n_s - 1))).  l, m, flux: FP64 device [n_src]; out: complex64 [n_vis].
+ */
+wst_status wst_predict_points(int64_t n_vis, const float *u, const float *v, const float *w,
+                              int64_t n_src, const double *l, const double *m, const double *flux,
+                              void *out, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WST_H */

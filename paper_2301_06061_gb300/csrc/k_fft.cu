@@ -1,0 +1,691 @@
+// K-F: per-plane centred 2D FFT (section 2, Eq. 2: the inner (u,v) integral; the paper
+// calls FFTW on the CPU for it, section 3.2), and K-P: the w-correction phase screen
+// and the reduction of the w-planes into the image, fused into the last FFT pass.
+//
+// Layout of the transform of an N x N plane (N = A * B, A >= B):
+//   pass R  : row FFTs of length N, one row (or several short rows) per CTA, whole row
+//             in shared memory, Stockham radix-16 stages with register butterflies.
+//   pass CA : four-step column stage A: for each a < A the length-B DFT over the rows
+//             a + A*b, then the twiddle w_N^{a c}; in place.  16-column bands.
+//   pass CB : four-step column stage B: for each c < B the length-A DFT over the
+//             contiguous rows A*c + a, giving output rows c + B*d.  Forward direction:
+//             the result never goes back to memory -- each CTA multiplies it by the
+//             centring sign, the phase screen of every plane of the chunk and adds it
+//             (Kahan-compensated) into the image tile it owns.
+// The centring (-1)^(p+q) is applied by the gridder's store (or the row pass for the
+// staged API) and (-1)^(a+b) in the CB epilogue.  The adjoint runs the conjugate
+// transposes in reverse order: CB^H (image tile -> plane rows, conjugate screen,
+// correction and sign fused), CA^H (twiddle first), row pass with the (-1)^(p+q) sign.
+//
+// Twiddles come from one table exp(+2 pi i m/N) rounded once from FP64; every
+// sub-length L divides N, so w_L^m = tw[m N/L].
+#include "wst_internal.cuh"
+
+namespace wst {
+
+// ---------------------------------------------------------------------------------
+// register DFTs of radix 2, 4, 8, 16 (natural order in and out), sign DIR
+// ---------------------------------------------------------------------------------
+constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
+constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {  // a * (DIR * i)
+  return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// a * exp(DIR * 2 pi i k / 16), k a compile-time constant in [0, 16)
+template <int DIR, int K>
+__device__ __forceinline__ float2 mul_w16(float2 a) {
+  constexpr int k = K & 15;
+  if constexpr (k == 0) return a;
+  else if constexpr (k == 4) return mul_i<DIR>(a);
+  else if constexpr (k == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (k == 12) return mul_i<-DIR>(a);
+  else {
+    // cos / sin of 2 pi k / 16 from the three constants
+    constexpr float cs[16] = {1.0f, kC16, kC8, kS16, 0.0f, -kS16, -kC8, -kC16,
+                              -1.0f, -kC16, -kC8, -kS16, 0.0f, kS16, kC8, kC16};
+    constexpr float c = cs[k];
+    constexpr float s = cs[(k + 12) & 15];  // sin(x) = cos(x - pi/2)
+    const float sd = DIR > 0 ? s : -s;
+    return make_float2(a.x * c - a.y * sd, a.x * sd + a.y * c);
+  }
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+  const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_i<DIR>(csub(b, d));
+  a = cadd(t0, t2);
+  c = csub(t0, t2);
+  b = cadd(t1, t3);
+  d = csub(t1, t3);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2 *v) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<DIR>(e0, e1, e2, e3);
+    dft4<DIR>(o0, o1, o2, o3);
+    o1 = mul_w16<DIR, 2>(o1);
+    o2 = mul_w16<DIR, 4>(o2);
+    o3 = mul_w16<DIR, 6>(o3);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+  } else {
+    static_assert(R == 16, "radix");
+    // 16 = 4 x 4: inputs r1 + 4 r2, outputs m2 + 4 m1
+    float2 y[16];
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) {
+      float2 a = v[r1], b = v[r1 + 4], c = v[r1 + 8], d = v[r1 + 12];
+      dft4<DIR>(a, b, c, d);
+      y[r1 * 4 + 0] = a;
+      y[r1 * 4 + 1] = b;
+      y[r1 * 4 + 2] = c;
+      y[r1 * 4 + 3] = d;
+    }
+    y[5] = mul_w16<DIR, 1>(y[5]);
+    y[6] = mul_w16<DIR, 2>(y[6]);
+    y[7] = mul_w16<DIR, 3>(y[7]);
+    y[9] = mul_w16<DIR, 2>(y[9]);
+    y[10] = mul_w16<DIR, 4>(y[10]);
+    y[11] = mul_w16<DIR, 6>(y[11]);
+    y[13] = mul_w16<DIR, 3>(y[13]);
+    y[14] = mul_w16<DIR, 6>(y[14]);
+    y[15] = mul_w16<DIR, 9>(y[15]);
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2) {
+      float2 a = y[0 * 4 + m2], b = y[1 * 4 + m2], c = y[2 * 4 + m2], d = y[3 * 4 + m2];
+      dft4<DIR>(a, b, c, d);
+      v[m2 + 0] = a;
+      v[m2 + 4] = b;
+      v[m2 + 8] = c;
+      v[m2 + 12] = d;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Stockham stage schedule for a length-L line with EPT elements per thread
+// ---------------------------------------------------------------------------------
+constexpr int stage_radix(int L, int ept, int s) {
+  int rem = L;
+  for (int i = 0; i < s; ++i) rem /= (rem < ept ? rem : ept);
+  return rem < ept ? rem : ept;
+}
+constexpr int stage_ns(int L, int ept, int s) {  // product of the radices before stage s
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= stage_radix(L, ept, i);
+  return ns;
+}
+constexpr int num_stages(int L, int ept) {
+  int n = 0, rem = L;
+  while (rem > 1) {
+    rem /= (rem < ept ? rem : ept);
+    ++n;
+  }
+  return n;
+}
+
+__device__ __forceinline__ float2 twiddle(const float2 *tw, int idx, int dir) {
+  float2 w = __ldg(tw + idx);
+  if (dir < 0) w.y = -w.y;
+  return w;
+}
+
+// Butterfly b of this thread has index j = jt + b * TPL (< L/R); its inputs sit at
+// j + r L/R and, after the twiddles w_{NS R}^{(j mod NS) r} and the radix-R DFT, its
+// outputs belong at (j / NS) NS R + (j mod NS) + r NS.
+template <int L, int EPT, int TPL, int S, int DIR>
+__device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const float2 *tw, int twscale) {
+  constexpr int R = stage_radix(L, EPT, S);
+  constexpr int NS = stage_ns(L, EPT, S);
+#pragma unroll
+  for (int b = 0; b < EPT / R; ++b) {
+    const int j = jt + b * TPL;
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const int m = k * r * (L / (NS * R));
+        v[b * R + r] = cmul(v[b * R + r], twiddle(tw, m * twscale, DIR));
+      }
+    }
+    dft<R, DIR>(&v[b * R]);
+  }
+}
+
+template <int L, int EPT, int TPL, int S>
+__device__ __forceinline__ int in_index(int jt, int b, int r) {
+  constexpr int R = stage_radix(L, EPT, S);
+  return jt + b * TPL + r * (L / R);
+}
+template <int L, int EPT, int TPL, int S>
+__device__ __forceinline__ int out_index(int jt, int b, int r) {
+  constexpr int R = stage_radix(L, EPT, S);
+  constexpr int NS = stage_ns(L, EPT, S);
+  const int j = jt + b * TPL;
+  return (j / NS) * NS * R + (j % NS) + r * NS;
+}
+
+// Run stages 1 .. last-1 through shared memory; `smi` maps a line index to a shared
+// memory slot.  On entry v holds the outputs of stage 0 (not yet stored); on return v
+// holds the inputs of the last stage, already loaded.
+template <int L, int EPT, int TPL, int S, int DIR, class SMI>
+__device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *sm, SMI smi,
+                                              const float2 *tw, int twscale) {
+  constexpr int NST = num_stages(L, EPT);
+  if constexpr (S < NST) {
+    // store outputs of stage S-1
+    constexpr int RP = stage_radix(L, EPT, S - 1);
+#pragma unroll
+    for (int b = 0; b < EPT / RP; ++b)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) sm[smi(out_index<L, EPT, TPL, S - 1>(jt, b, r))] = v[b * RP + r];
+    __syncthreads();
+    constexpr int R = stage_radix(L, EPT, S);
+#pragma unroll
+    for (int b = 0; b < EPT / R; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = sm[smi(in_index<L, EPT, TPL, S>(jt, b, r))];
+    if constexpr (S + 1 < NST) {
+      __syncthreads();  // every load of this stage done before the next stores
+      stage_compute<L, EPT, TPL, S, DIR>(v, jt, tw, twscale);
+      middle_stages<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, tw, twscale);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// pass R: row FFTs
+// ---------------------------------------------------------------------------------
+template <int N>
+struct RowCfg {
+  static constexpr int EPT = N >= 16 ? 16 : N;
+  static constexpr int TPR = N / EPT;
+  static constexpr int RPC = TPR >= 256 ? 1 : 256 / TPR;
+  static constexpr int THREADS = TPR * RPC;
+  static constexpr int PADL = N + N / 16;
+};
+
+template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS)
+k_rows(float2 *__restrict__ planes, const float2 *__restrict__ tw) {
+  using C = RowCfg<N>;
+  constexpr int EPT = C::EPT, TPR = C::TPR;
+  constexpr int NST = num_stages(N, EPT);
+  extern __shared__ float2 sm_rows[];
+  const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
+  const int q = blockIdx.x * C::RPC + rl;
+  float2 *row = planes + ((size_t)blockIdx.y * N + q) * N;
+  float2 *srow = sm_rows + rl * C::PADL;
+  auto smi = [](int i) { return i + (i >> 4); };
+  float2 v[EPT];
+  constexpr int R0 = stage_radix(N, EPT, 0);
+#pragma unroll
+  for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+      float2 x = row[idx];
+      if (PRESIGN && ((idx + q) & 1)) x = make_float2(-x.x, -x.y);
+      v[b * R0 + r] = x;
+    }
+  stage_compute<N, EPT, TPR, 0, DIR>(v, jt, tw, 1);
+  if constexpr (NST > 1) {
+    middle_stages<N, EPT, TPR, 1, DIR>(v, jt, srow, smi, tw, 1);
+    stage_compute<N, EPT, TPR, NST - 1, DIR>(v, jt, tw, 1);
+  }
+  constexpr int RL = stage_radix(N, EPT, NST - 1);
+#pragma unroll
+  for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int idx = out_index<N, EPT, TPR, NST - 1>(jt, b, r);
+      float2 x = v[b * RL + r];
+      if (POSTSIGN && ((idx + q) & 1)) x = make_float2(-x.x, -x.y);
+      row[idx] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// pass CA: four-step column stage A, length-LB lines over rows a + A*i, 16-col bands
+// ---------------------------------------------------------------------------------
+constexpr int kCB = 16;  // columns per band (128 bytes per row segment)
+
+template <int L>
+struct ColCfg {
+  static constexpr int EPT = L >= 8 ? 8 : L;
+  static constexpr int TPL = L / EPT;
+  static constexpr int THREADS = TPL * kCB;
+  static constexpr int PADW = kCB + 1;  // smem row stride (float2)
+};
+
+template <int LB, int DIR, bool TW_FIRST>
+__global__ void __launch_bounds__(ColCfg<LB>::THREADS)
+k_cols_a(float2 *__restrict__ planes, const float2 *__restrict__ tw, int n) {
+  using C = ColCfg<LB>;
+  constexpr int EPT = C::EPT, TPL = C::TPL;
+  constexpr int NST = num_stages(LB, EPT);
+  __shared__ float2 sm[LB * C::PADW];
+  const int A = n / LB;
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int a = blockIdx.y;
+  const int kp = blockIdx.x * kCB + col;
+  float2 *base = planes + (size_t)blockIdx.z * n * n + kp;
+  const size_t rstride = (size_t)A * n;  // line element i -> row a + A*i
+  base += (size_t)a * n;
+  auto smi = [col](int i) { return i * C::PADW + col; };
+  float2 v[EPT];
+  constexpr int R0 = stage_radix(LB, EPT, 0);
+#pragma unroll
+  for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int i = in_index<LB, EPT, TPL, 0>(jt, b, r);
+      float2 x = base[(size_t)i * rstride];
+      if (TW_FIRST) x = cmul(x, twiddle(tw, a * i, DIR));
+      v[b * R0 + r] = x;
+    }
+  stage_compute<LB, EPT, TPL, 0, DIR>(v, jt, tw, A);
+  if constexpr (NST > 1) {
+    middle_stages<LB, EPT, TPL, 1, DIR>(v, jt, sm, smi, tw, A);
+    stage_compute<LB, EPT, TPL, NST - 1, DIR>(v, jt, tw, A);
+  }
+  constexpr int RL = stage_radix(LB, EPT, NST - 1);
+#pragma unroll
+  for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int c = out_index<LB, EPT, TPL, NST - 1>(jt, b, r);
+      float2 x = v[b * RL + r];
+      if (!TW_FIRST) x = cmul(x, twiddle(tw, a * c, DIR));
+      base[(size_t)c * rstride] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// phase screen helpers (K-P)
+// ---------------------------------------------------------------------------------
+struct ScreenCtx {
+  const float2 *l2ff;      // l_a^2 float-float
+  const double *l2d;       // l_a^2 FP64
+  const float2 *wc;        // plane centres float-float (global plane index)
+  const double *wcd;       // plane centres FP64
+  const float *corr;       // 1/Ghat
+  int fp64;                // WST_FLAG_FP64_SCREEN
+};
+
+struct PixelScreen {
+  ff t;      // n - 1
+  double td; // n - 1 in FP64 (fp64 mode)
+  bool valid;
+};
+
+__device__ __forceinline__ PixelScreen pixel_screen(const ScreenCtx &sc, int kp, int kq) {
+  PixelScreen ps;
+  const float2 la = sc.l2ff[kp], mb = sc.l2ff[kq];
+  ps.t = n_minus_one_ff(la, mb, ps.valid);
+  ps.td = 0.0;
+  if (sc.fp64 && ps.valid) {
+    const double r2 = sc.l2d[kp] + sc.l2d[kq];
+    ps.td = -r2 / (1.0 + sqrt(1.0 - r2));
+  }
+  return ps;
+}
+
+__device__ __forceinline__ float2 screen_value(const ScreenCtx &sc, const PixelScreen &ps, int P) {
+  if (!ps.valid) return make_float2(0.0f, 0.0f);
+  if (sc.fp64) return cis_cycles_d(sc.wcd[P] * ps.td);
+  const float2 w = sc.wc[P];
+  return cis_cycles_ff(ff_mul({w.x, w.y}, ps.t));
+}
+
+__device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 y) {
+  const float yx = __fsub_rn(y.x, c.x), yy = __fsub_rn(y.y, c.y);
+  const float tx = __fadd_rn(s.x, yx), ty = __fadd_rn(s.y, yy);
+  c.x = __fsub_rn(__fsub_rn(tx, s.x), yx);
+  c.y = __fsub_rn(__fsub_rn(ty, s.y), yy);
+  s.x = tx;
+  s.y = ty;
+}
+
+// epilogue modes
+enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
+
+// ---------------------------------------------------------------------------------
+// pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then sign, screen and the
+// compensated sum over the chunk's planes into the image.
+// ---------------------------------------------------------------------------------
+template <int LA>
+__global__ void __launch_bounds__(ColCfg<LA>::THREADS)
+k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const float2 *__restrict__ tw,
+             int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
+  using C = ColCfg<LA>;
+  constexpr int EPT = C::EPT, TPL = C::TPL;
+  constexpr int NST = num_stages(LA, EPT);
+  constexpr int RL = stage_radix(LA, EPT, NST - 1);
+  constexpr int R0 = stage_radix(LA, EPT, 0);
+  __shared__ float2 sm[LA * C::PADW];
+  const int B = n / LA;
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int c = blockIdx.y;
+  const int kp = blockIdx.x * kCB + col;
+  auto smi = [col](int i) { return i * C::PADW + col; };
+  // this thread's output pixels: d = out_index(...), kq = c + B d
+  PixelScreen px[EPT];
+  float sgn[EPT];
+#pragma unroll
+  for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int d = out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
+      const int kq = c + B * d;
+      px[b * RL + r] = pixel_screen(sc, kp, kq);
+      sgn[b * RL + r] = ((kq + kp) & 1) ? -1.0f : 1.0f;
+    }
+  const bool kahan = flags & ACC_KAHAN;
+  int P = p0;
+  while (P < p1) {
+    const int img = P / n_w;
+    const int pend = min(p1, (img + 1) * n_w);
+    float2 s[EPT], cc[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) s[e] = cc[e] = make_float2(0.0f, 0.0f);
+    for (; P < pend; ++P) {
+      const float2 *base = planes + (size_t)(P - p0) * n * n + (size_t)(LA * c) * n + kp;
+      float2 v[EPT];
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[b * R0 + r] = base[(size_t)in_index<LA, EPT, TPL, 0>(jt, b, r) * n];
+      stage_compute<LA, EPT, TPL, 0, 1>(v, jt, tw, B);
+      if constexpr (NST > 1) {
+        middle_stages<LA, EPT, TPL, 1, 1>(v, jt, sm, smi, tw, B);
+        stage_compute<LA, EPT, TPL, NST - 1, 1>(v, jt, tw, B);
+      }
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float2 y = cmul(v[e], screen_value(sc, px[e], P));
+        const float2 ys = make_float2(sgn[e] * y.x, sgn[e] * y.y);
+        if (kahan) kahan_add(s[e], cc[e], ys);
+        else s[e] = cadd(s[e], ys);
+      }
+      if constexpr (NST > 1) __syncthreads();  // shared memory reused by the next plane
+    }
+    // flush this image's tile: its sum starts in this chunk if its first plane is at
+    // or after p0, and is complete if its last plane is before p1
+    const bool first_any = img * n_w >= p0;
+    const bool last_any = (img + 1) * n_w <= p1;
+    float2 *im = image + (size_t)img * n * n;
+    float2 *cp = comp ? comp + (size_t)img * n * n : nullptr;
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int e = b * RL + r;
+        const int d = out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
+        const size_t o = (size_t)(c + B * d) * n + kp;
+        float2 sum = s[e], cmp = cc[e];
+        if (flags & ACC_STAGED) {
+          float2 old = im[o];
+          im[o] = cadd(old, csub(sum, cmp));
+          continue;
+        }
+        if (!first_any) {  // merge with the running (sum, compensation) of earlier chunks
+          const float2 s0 = im[o];
+          const float2 c0 = cp ? cp[o] : make_float2(0.0f, 0.0f);
+          float2 acc_s = s0, acc_c = c0;
+          kahan_add(acc_s, acc_c, sum);
+          float2 negc = make_float2(-cmp.x, -cmp.y);
+          kahan_add(acc_s, acc_c, negc);
+          sum = acc_s;
+          cmp = acc_c;
+        }
+        if (last_any) {
+          float2 out = csub(sum, cmp);
+          if (flags & ACC_CORRECT) {
+            const float f = sc.corr[kp] * sc.corr[c + B * d];
+            out = make_float2(out.x * f, out.y * f);
+          }
+          im[o] = out;
+        } else {
+          im[o] = sum;
+          if (cp) cp[o] = cmp;
+        }
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// pass CB^H (adjoint): image tile -> planes; sign, correction and conjugate screen fused
+// ---------------------------------------------------------------------------------
+template <int LA>
+__global__ void __launch_bounds__(ColCfg<LA>::THREADS)
+k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, const float2 *__restrict__ tw,
+          int n, ScreenCtx sc, int correct, float2 *__restrict__ planes) {
+  using C = ColCfg<LA>;
+  constexpr int EPT = C::EPT, TPL = C::TPL;
+  constexpr int NST = num_stages(LA, EPT);
+  constexpr int RL = stage_radix(LA, EPT, NST - 1);
+  constexpr int R0 = stage_radix(LA, EPT, 0);
+  __shared__ float2 sm[LA * C::PADW];
+  const int B = n / LA;
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int c = blockIdx.y;
+  const int kp = blockIdx.x * kCB + col;
+  auto smi = [col](int i) { return i * C::PADW + col; };
+  // inputs of the first stage: element d <-> image row kq = c + B d
+  PixelScreen px[EPT];
+  float scale[EPT];
+  float2 dv[EPT];
+  int img_loaded = -1;
+#pragma unroll
+  for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      const int d = in_index<LA, EPT, TPL, 0>(jt, b, r);
+      const int kq = c + B * d;
+      px[b * R0 + r] = pixel_screen(sc, kp, kq);
+      float f = ((kq + kp) & 1) ? -1.0f : 1.0f;
+      if (correct) f *= sc.corr[kp] * sc.corr[kq];
+      scale[b * R0 + r] = f;
+    }
+  for (int P = p0; P < p1; ++P) {
+    const int img = P / n_w;
+    if (img != img_loaded) {
+      const float2 *im = dimage + (size_t)img * n * n;
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int d = in_index<LA, EPT, TPL, 0>(jt, b, r);
+          dv[b * R0 + r] = im[(size_t)(c + B * d) * n + kp];
+        }
+      img_loaded = img;
+    }
+    float2 v[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const float2 y = cmulc(dv[e], screen_value(sc, px[e], P));  // conj(screen) * D
+      v[e] = make_float2(scale[e] * y.x, scale[e] * y.y);
+    }
+    stage_compute<LA, EPT, TPL, 0, -1>(v, jt, tw, B);
+    if constexpr (NST > 1) {
+      middle_stages<LA, EPT, TPL, 1, -1>(v, jt, sm, smi, tw, B);
+      stage_compute<LA, EPT, TPL, NST - 1, -1>(v, jt, tw, B);
+    }
+    float2 *base = planes + (size_t)(P - p0) * n * n + (size_t)(LA * c) * n + kp;
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) base[(size_t)out_index<LA, EPT, TPL, NST - 1>(jt, b, r) * n] = v[b * RL + r];
+    if constexpr (NST > 1) __syncthreads();
+  }
+}
+
+// elementwise grid correction
+__global__ void k_correct(float2 *image, const float *corr, int n, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pix = i % ((int64_t)n * n);
+    const int a = (int)(pix % n), b = (int)(pix / n);
+    const float f = corr[a] * corr[b];
+    float2 x = image[i];
+    image[i] = make_float2(x.x * f, x.y * f);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// host dispatch
+// ---------------------------------------------------------------------------------
+template <int N, int DIR, bool PRE, bool POST>
+static cudaError_t launch_rows(float2 *planes, int nplanes, const float2 *tw, cudaStream_t s) {
+  using C = RowCfg<N>;
+  const size_t smem = sizeof(float2) * C::RPC * C::PADL;
+  auto kern = k_rows<N, DIR, PRE, POST>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grd(N / C::RPC, nplanes);
+  kern<<<grd, C::THREADS, smem, s>>>(planes, tw);
+  return cudaGetLastError();
+}
+
+template <int DIR, bool PRE, bool POST>
+static cudaError_t rows_dispatch(int n, float2 *planes, int nplanes, const float2 *tw, cudaStream_t s) {
+  switch (n) {
+    case 64: return launch_rows<64, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 128: return launch_rows<128, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 256: return launch_rows<256, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 512: return launch_rows<512, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 1024: return launch_rows<1024, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 2048: return launch_rows<2048, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 4096: return launch_rows<4096, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 8192: return launch_rows<8192, DIR, PRE, POST>(planes, nplanes, tw, s);
+    case 16384: return launch_rows<16384, DIR, PRE, POST>(planes, nplanes, tw, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool presign, bool postsign) {
+  if (nplanes <= 0) return cudaSuccess;
+  if (dir > 0 && !presign && !postsign) return rows_dispatch<1, false, false>(p->n, planes, nplanes, p->tw, p->stream);
+  if (dir > 0 && presign && !postsign) return rows_dispatch<1, true, false>(p->n, planes, nplanes, p->tw, p->stream);
+  if (dir < 0 && !presign && postsign) return rows_dispatch<-1, false, true>(p->n, planes, nplanes, p->tw, p->stream);
+  return cudaErrorInvalidValue;
+}
+
+template <int LB, int DIR, bool TWF>
+static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes) {
+  dim3 grd(p->n / kCB, p->n / LB, nplanes);
+  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, p->tw, p->n);
+  return cudaGetLastError();
+}
+
+template <int DIR, bool TWF>
+static cudaError_t cols_a_dispatch(wst_plan_s *p, float2 *planes, int nplanes) {
+  switch (p->fb) {
+    case 8: return launch_cols_a<8, DIR, TWF>(p, planes, nplanes);
+    case 16: return launch_cols_a<16, DIR, TWF>(p, planes, nplanes);
+    case 32: return launch_cols_a<32, DIR, TWF>(p, planes, nplanes);
+    case 64: return launch_cols_a<64, DIR, TWF>(p, planes, nplanes);
+    case 128: return launch_cols_a<128, DIR, TWF>(p, planes, nplanes);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first) {
+  if (nplanes <= 0) return cudaSuccess;
+  if (dir > 0 && !twiddle_first) return cols_a_dispatch<1, false>(p, planes, nplanes);
+  if (dir < 0 && twiddle_first) return cols_a_dispatch<-1, true>(p, planes, nplanes);
+  return cudaErrorInvalidValue;
+}
+
+static ScreenCtx screen_ctx(wst_plan_s *p) {
+  ScreenCtx sc;
+  sc.l2ff = p->l2ff;
+  sc.l2d = p->l2d;
+  sc.wc = p->wcentre;
+  sc.wcd = p->wcentre_d;
+  sc.corr = p->corr;
+  sc.fp64 = (p->cfg.flags & WST_FLAG_FP64_SCREEN) ? 1 : 0;
+  return sc;
+}
+
+template <int LA>
+static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
+                                 float2 *comp, int flags) {
+  dim3 grd(p->n / kCB, p->n / LA);
+  k_cols_b_acc<LA><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, p->tw, p->n,
+                                                                screen_ctx(p), image, comp, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
+                                  float2 *comp, bool kahan, bool correct, bool staged_add) {
+  if (p1 <= p0) return cudaSuccess;
+  int flags = 0;
+  if (correct) flags |= ACC_CORRECT;
+  if (kahan) flags |= ACC_KAHAN;
+  if (staged_add) flags |= ACC_STAGED;
+  switch (p->fa) {
+    case 8: return launch_cols_b<8>(p, planes, p0, p1, image, comp, flags);
+    case 16: return launch_cols_b<16>(p, planes, p0, p1, image, comp, flags);
+    case 32: return launch_cols_b<32>(p, planes, p0, p1, image, comp, flags);
+    case 64: return launch_cols_b<64>(p, planes, p0, p1, image, comp, flags);
+    case 128: return launch_cols_b<128>(p, planes, p0, p1, image, comp, flags);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int LA>
+static cudaError_t launch_cols_bh(wst_plan_s *p, const float2 *dimage, int p0, int p1, float2 *planes,
+                                  bool correct) {
+  dim3 grd(p->n / kCB, p->n / LA);
+  k_cols_bh<LA><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, p->tw, p->n,
+                                                             screen_ctx(p), correct ? 1 : 0, planes);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_cols_bh_from_image(wst_plan_s *p, const float2 *dimage, int p0, int p1, float2 *planes,
+                                   bool correct) {
+  if (p1 <= p0) return cudaSuccess;
+  switch (p->fa) {
+    case 8: return launch_cols_bh<8>(p, dimage, p0, p1, planes, correct);
+    case 16: return launch_cols_bh<16>(p, dimage, p0, p1, planes, correct);
+    case 32: return launch_cols_bh<32>(p, dimage, p0, p1, planes, correct);
+    case 64: return launch_cols_bh<64>(p, dimage, p0, p1, planes, correct);
+    case 128: return launch_cols_bh<128>(p, dimage, p0, p1, planes, correct);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t correct_image(wst_plan_s *p, float2 *image) {
+  const int64_t total = (int64_t)p->batch * p->n * p->n;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_correct<<<(unsigned)blocks, 256, 0, p->stream>>>(image, p->corr, p->n, total);
+  return cudaGetLastError();
+}
+
+}  // namespace wst

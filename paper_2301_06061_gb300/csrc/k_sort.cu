@@ -1,0 +1,332 @@
+// K-S: device bucket sort of visibilities by (image, w-plane, 64x64 tile, spill class).
+//
+// Placement follows section 2 / Eq. 3: a visibility at x = N/2 + u FoV touches the W
+// cells i0 = ceil(x - W/2) ... i0 + W - 1 and goes to the closest w-plane.  x, the tap
+// start and the plane index are computed in FP64 with explicitly rounded operations
+// (no contraction), so they are the same numbers a plain double-precision program
+// gets.  The sub-cell offset g = i0 - (x - W/2) in [0,1) is then quantised to 24 bits.
+//
+// Buckets replace the paper's per-slab linked lists (section 3.2): both exist to give
+// the gridding kernel contiguous visibilities for one region of the mesh.  A record
+// is filed under the tile that holds its tap start; the spill class says whether its
+// footprint crosses into the right (x) and/or lower (y) neighbour tile, so that a tile
+// owner can read exactly the neighbour records that reach into it:
+//   class 0: none, 1: x only, 2: x and y, 3: y only
+// (left neighbour needs classes 1..2, upper neighbour 2..3, upper-left neighbour 2).
+#include "wst_internal.cuh"
+
+namespace wst {
+
+__device__ __forceinline__ uint32_t float_to_ordered(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+__device__ __forceinline__ void warp_count(unsigned long long *ctr, bool pred) {
+  unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+// per image min / max of the finite w (order-preserving integer encoding)
+__global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax) {
+  const int img = blockIdx.y;
+  const int64_t b0 = boff[img], b1 = boff[img + 1];
+  uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+  for (int64_t j = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b1;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float x = w[j];
+    if (isfinite(x)) {
+      uint32_t o = float_to_ordered(x);
+      mn = min(mn, o);
+      mx = max(mx, o);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, s));
+    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, s));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mn != 0xFFFFFFFFu) atomicMin(&wminmax[2 * img], mn);
+    if (mx != 0u) atomicMax(&wminmax[2 * img + 1], mx);
+  }
+}
+
+struct SortGeom {
+  int n, W, tiles, n_w;
+  double half_n, half_w, fov;
+};
+
+// pass 1: placement, bucket key, histogram rank (warp-aggregated atomics)
+__global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
+                       const float *__restrict__ w, const float2 *__restrict__ vis,
+                       const float *__restrict__ weight, const int64_t *__restrict__ boff,
+                       const double *__restrict__ wrange, SortGeom g, uint32_t *offsets,
+                       uint4 *keyinfo, unsigned long long *counters) {
+  const int img = blockIdx.y;
+  const int64_t b0 = boff[img], b1 = boff[img + 1];
+  const double w_lo = wrange[4 * img + 0];
+  const double scale = wrange[4 * img + 1];
+  const int64_t span = b1 - b0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // uniform trip count across the warp so that the warp-level votes are safe
+  const int64_t start = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t base = start; base < span; base += stride) {
+    const int64_t jj = base + (threadIdx.x & 31);
+    const bool in = jj < span;
+    const int64_t j = b0 + jj;
+    bool nonfinite = false, dropped = false, kept = false;
+    uint32_t key = kDropKey, xpack = 0, ypack = 0;
+    if (in) {
+      const float uf = u[j], vf = v[j], wf = w[j];
+      const float2 val = vis[j];
+      const float wt = weight ? weight[j] : 1.0f;
+      if (!(isfinite(uf) && isfinite(vf) && isfinite(wf) && finite2(val) && isfinite(wt))) {
+        nonfinite = true;
+      } else {
+        const double x = __dadd_rn(g.half_n, __dmul_rn((double)uf, g.fov));
+        const double y = __dadd_rn(g.half_n, __dmul_rn((double)vf, g.fov));
+        const double hx = __dsub_rn(x, g.half_w), hy = __dsub_rn(y, g.half_w);
+        const double ci = ceil(hx), cj = ceil(hy);
+        if (ci < 0.0 || cj < 0.0 || ci + g.W > g.n || cj + g.W > g.n) {
+          dropped = true;
+        } else {
+          int k = 0;
+          if (scale > 0.0) {
+            const double q = floor(__dmul_rn(__dsub_rn((double)wf, w_lo), scale));
+            k = q < 0.0 ? 0 : (q > g.n_w - 1 ? g.n_w - 1 : (int)q);
+          }
+          const int i0 = (int)ci, j0 = (int)cj;
+          // exact offsets in [0, 1), quantised to 2^-24 (round to nearest, kept below 1)
+          const double gx = __dsub_rn(ci, hx), gy = __dsub_rn(cj, hy);
+          uint32_t fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
+          uint32_t fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
+          const int tx = i0 >> kLogTile, ty = j0 >> kLogTile;
+          const int cx = i0 & (kTile - 1), cy = j0 & (kTile - 1);
+          const bool sx = cx > kTile - g.W, sy = cy > kTile - g.W;
+          const int cls = sx ? (sy ? 2 : 1) : (sy ? 3 : 0);
+          key = (uint32_t)(((((int64_t)img * g.n_w + k) * g.tiles + ty) * g.tiles + tx) * kClasses + cls);
+          xpack = ((uint32_t)cx << kFracBits) | fx;
+          ypack = ((uint32_t)cy << kFracBits) | fy;
+          kept = true;
+        }
+      }
+    }
+    // warp-aggregated histogram: one atomic per distinct key in the warp
+    const unsigned active = __ballot_sync(0xFFFFFFFFu, kept);
+    uint32_t rank = 0;
+    if (kept) {
+      const unsigned peers = __match_any_sync(active, key);
+      const int leader = __ffs(peers) - 1;
+      const int lane = threadIdx.x & 31;
+      uint32_t base_rank = 0;
+      if (lane == leader) base_rank = atomicAdd(&offsets[key], (uint32_t)__popc(peers));
+      base_rank = __shfl_sync(peers, base_rank, leader);
+      rank = base_rank + __popc(peers & ((1u << lane) - 1u));
+    }
+    if (in) keyinfo[j] = make_uint4(key, rank, xpack, ypack);
+    warp_count(&counters[CNT_KEPT], kept);
+    warp_count(&counters[CNT_DROPPED], dropped);
+    warp_count(&counters[CNT_NONFINITE], nonfinite);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// exclusive scan of uint32 counts, in place, multi-level (4096 items per block)
+// ---------------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total) {
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = x;
+  for (int s = 1; s < 32; s <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, s);
+    if (lane >= s) incl += y;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t ws = warp_sums[lane];
+    uint32_t wi = ws;
+    for (int s = 1; s < 32; s <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, s);
+      if (lane >= s) wi += y;
+    }
+    warp_sums[lane] = wi - ws;  // exclusive warp offsets
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  const uint32_t r = warp_sums[wid] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t *data, int64_t n, uint32_t *block_sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += data[base + i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  __shared__ uint32_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = ws[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan_apply(uint32_t *data, int64_t n, const uint32_t *block_offsets) {
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? data[base + i] : 0u;
+    s += v[i];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, &total) + (block_offsets ? block_offsets[blockIdx.x] : 0u);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) data[base + i] = run;
+    run += v[i];
+  }
+}
+
+static int64_t scan_blocks(int64_t n) { return (n + kScanBlock - 1) / kScanBlock; }
+
+int64_t scan_tmp_words(int64_t n) {
+  int64_t words = 0;
+  while (n > 1) {
+    n = scan_blocks(n);
+    words += n + 64;
+  }
+  return words + 64;
+}
+
+static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cudaStream_t s) {
+  const int64_t nb = scan_blocks(n);
+  if (nb <= 1) {
+    k_scan_apply<<<1, kScanThreads, 0, s>>>(data, n, nullptr);
+    return cudaGetLastError();
+  }
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, tmp);
+  cudaError_t e = scan_exclusive(tmp, nb, tmp + nb + 64, s);
+  if (e != cudaSuccess) return e;
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, tmp);
+  return cudaGetLastError();
+}
+
+// pass 2: scatter records to their sorted position
+__global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
+                          const uint4 *__restrict__ keyinfo, const uint32_t *__restrict__ offsets,
+                          int64_t n_vis, Record *records, uint32_t *perm, float *rweight) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_vis;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 ki = keyinfo[j];
+    if (ki.x == kDropKey) continue;
+    const uint32_t pos = offsets[ki.x] + ki.y;
+    const float2 val = vis[j];
+    const float wt = weight ? weight[j] : 1.0f;
+    Record r;
+    r.xpack = ki.z;
+    r.ypack = ki.w;
+    r.vre = val.x * wt;
+    r.vim = val.y * wt;
+    records[pos] = r;
+    perm[pos] = (uint32_t)j;
+    if (rweight) rweight[pos] = wt;
+  }
+}
+
+static unsigned grid_for(int64_t n, int threads, int max_blocks) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > max_blocks) b = max_blocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
+                              const float2 *vis, const float *weight) {
+  cudaStream_t s = p->stream;
+  Workspace &ws = p->W_;
+  const int64_t nb1 = p->n_buckets + 1;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.counters, 0, sizeof(unsigned long long) * CNT_SLOTS, s))) return e;
+  if ((e = cudaMemsetAsync(ws.offsets, 0, sizeof(uint32_t) * nb1, s))) return e;
+  // w range of each image (only consulted when the config leaves it to the data)
+  if ((e = cudaMemsetAsync(ws.wminmax, 0, sizeof(uint32_t) * 2 * p->batch, s))) return e;
+  for (int i = 0; i < p->batch; ++i) {  // min slots start at all-ones
+    if ((e = cudaMemsetAsync(ws.wminmax + 2 * i, 0xFF, sizeof(uint32_t), s))) return e;
+  }
+  const int64_t avg = p->n_vis / p->batch + 1;
+  dim3 grd(grid_for(avg, 256, 4096), p->batch);
+  if (p->cfg.w_min == p->cfg.w_max) k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax);
+  if ((e = build_plane_centres(p))) return e;
+  SortGeom g;
+  g.n = p->n;
+  g.W = p->W;
+  g.tiles = p->tiles;
+  g.n_w = p->n_w;
+  g.half_n = 0.5 * p->n;
+  g.half_w = 0.5 * p->W;
+  g.fov = p->cfg.fov;
+  k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, g, ws.offsets,
+                               ws.keyinfo, ws.counters);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s))) return e;
+  k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(
+      vis, weight, ws.keyinfo, ws.offsets, p->n_vis, ws.records, ws.perm,
+      weight ? ws.rweight : nullptr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// per-visibility placement read back from the sorted records (inspection call)
+// ---------------------------------------------------------------------------------
+__global__ void k_vis_cells(const Record *rec, const uint32_t *perm, const uint32_t *offsets,
+                            int64_t n_buckets, int64_t n_bound, int tiles, int n_w,
+                            int32_t *plane, int32_t *i0, int32_t *j0) {
+  const int64_t n_kept = offsets[n_buckets];  // records beyond it are not written
+  const int64_t n_iter = n_kept < n_bound ? n_kept : n_bound;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_iter;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    // bucket = last b with offsets[b] <= s
+    int64_t lo = 0, hi = n_buckets;  // offsets[lo] <= s < offsets[hi]
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (offsets[mid] <= (uint32_t)s) lo = mid; else hi = mid;
+    }
+    const int64_t key = lo / kClasses;
+    const int tx = (int)(key % tiles);
+    const int ty = (int)((key / tiles) % tiles);
+    const int k = (int)((key / ((int64_t)tiles * tiles)) % n_w);
+    const Record r = rec[s];
+    const uint32_t j = perm[s];
+    plane[j] = k;
+    i0[j] = tx * kTile + (int)(r.xpack >> kFracBits);
+    j0[j] = ty * kTile + (int)(r.ypack >> kFracBits);
+  }
+}
+
+cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, int64_t n_bound) {
+  cudaStream_t s = p->stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(plane, 0xFF, sizeof(int32_t) * p->n_vis, s))) return e;
+  if ((e = cudaMemsetAsync(i0, 0xFF, sizeof(int32_t) * p->n_vis, s))) return e;
+  if ((e = cudaMemsetAsync(j0, 0xFF, sizeof(int32_t) * p->n_vis, s))) return e;
+  if (n_bound > 0)
+    k_vis_cells<<<grid_for(n_bound, 256, 152 * 16), 256, 0, s>>>(
+        p->W_.records, p->W_.perm, p->W_.offsets, p->n_buckets, n_bound, p->tiles, p->n_w, plane,
+        i0, j0);
+  return cudaGetLastError();
+}
+
+}  // namespace wst

@@ -1,0 +1,246 @@
+// Internal declarations shared by the libwst translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "wst.h"
+
+namespace wst {
+
+constexpr int kTile = 64;        // gridding tile side (cells)
+constexpr int kLogTile = 6;
+constexpr int kClasses = 4;      // spill classes per tile bucket (see k_sort.cu)
+constexpr int kMaxSupport = 16;  // W <= 16: one warp evaluates both 1D kernel profiles
+constexpr uint32_t kDropKey = 0xFFFFFFFFu;
+constexpr int kFracBits = 24;    // sub-cell offset quantisation: 2^-24 cell
+
+// counters[] slots in the workspace
+enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_SLOTS = 8 };
+
+// 16-byte sorted record: tap start within its tile (8 bits) and the sub-cell
+// offset g = i0 - (x - W/2) in [0,1) quantised to 24 bits, per axis; weighted value.
+struct __align__(16) Record {
+  uint32_t xpack;
+  uint32_t ypack;
+  float vre;
+  float vim;
+};
+
+struct KernelParams {
+  int kind;        // WST_KERNEL_*
+  int support;     // W
+  float half;      // W/2
+  float inv2s2;    // GAUSS: 1/(2 sigma^2)
+  float beta;      // ES
+  float two_over_w;
+  const float *table;  // TABLE: device samples
+  int table_len;
+  float table_scale;   // (L-1)/W
+};
+
+struct Workspace {
+  uint4 *keyinfo;      // per visibility: key, rank, xpack, ypack (aliases the plane buffer)
+  Record *records;     // sorted records
+  uint32_t *perm;      // sorted position -> caller index
+  float *rweight;      // sorted position -> weight (only when weights are given)
+  uint32_t *offsets;   // bucket offsets [n_buckets + 1]
+  uint32_t *scan_tmp;  // scan partial sums
+  unsigned long long *counters;  // CNT_* slots
+  uint32_t *wminmax;   // per image: ordered-int min and max of finite w
+  float2 *planes;      // chunk of planes
+  float2 *comp;        // Kahan compensation image [batch][N*N]
+  size_t bytes;
+};
+
+}  // namespace wst
+
+struct wst_plan_s {
+  wst_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // geometry
+  int n = 0, log2n = 0, W = 0, tiles = 0, n_w = 0, batch = 1, n_planes = 0, chunk = 0;
+  int fa = 0, fb = 0;  // four-step column split N = fa * fb (fa contiguous block rows)
+  int64_t n_buckets = 0;
+  // owned device tables
+  float2 *tw = nullptr;      // exp(+2 pi i m / N), m < N
+  float *corr = nullptr;     // 1 / Ghat(nu_a)
+  float2 *l2ff = nullptr;    // l_a^2 as float-float
+  double *l2d = nullptr;     // l_a^2 in FP64 (WST_FLAG_FP64_SCREEN)
+  float *ktable = nullptr;   // TABLE kernel samples
+  double *wrange = nullptr;  // per image: w_lo, scale = n_w/(w_hi-w_lo), dw, w_hi
+  float2 *wcentre = nullptr; // per global plane: centre w_k as float-float
+  double *wcentre_d = nullptr;  // per global plane: centre w_k (FP64)
+  bool table_set = false;
+  // workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  wst::Workspace W_;
+  int64_t n_vis = 0;
+  bool vis_set = false;
+  bool has_weight = false;
+  int64_t *batch_off = nullptr;  // device copy of batch offsets [batch+1]
+  // timing
+  cudaEvent_t ev[6] = {};
+  bool timing = false;
+  float ms[5] = {0, 0, 0, 0, 0};
+  bool ms_pending = false;
+  int n_chunks = 0;
+  std::string last_error;
+};
+
+namespace wst {
+
+// ------------------------------------------------------------------------------------
+// error-free float transforms and float-float ("double-single") arithmetic
+// (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2)
+// ------------------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+  ff s = two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  ff p = two_prod(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  return quick_two_sum(p.hi, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff x) {  // x.hi > 0
+  float s = __fsqrt_rn(x.hi);
+  ff p = two_prod(s, s);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
+  return quick_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+  float q1 = __fdiv_rn(x.hi, y.hi);
+  ff p = ff_mul({q1, 0.0f}, y);
+  ff r = ff_add(x, ff_neg(p));
+  float q2 = __fdiv_rn(r.hi, y.hi);
+  return quick_two_sum(q1, q2);
+}
+__host__ __device__ __forceinline__ float2 ff_split(double d) {
+  float hi = (float)d;
+  float lo = (float)(d - (double)hi);
+  return make_float2(hi, lo);
+}
+
+// n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)) in float-float; valid = l^2+m^2 < 1
+__device__ __forceinline__ ff n_minus_one_ff(float2 l2, float2 m2, bool &valid) {
+  ff r2 = ff_add({l2.x, l2.y}, {m2.x, m2.y});
+  valid = r2.hi < 1.0f;
+  if (!valid) return {0.0f, 0.0f};
+  ff om = ff_add({1.0f, 0.0f}, ff_neg(r2));
+  ff s = ff_sqrt(om);
+  ff den = ff_add({1.0f, 0.0f}, s);
+  return ff_neg(ff_div(r2, den));
+}
+
+// exp(2 pi i phi) for a float-float phase in cycles: reduce modulo one cycle exactly
+// in the high word, then FP32 sincospi of the small remainder.
+__device__ __forceinline__ float2 cis_cycles_ff(ff phi) {
+  float n = rintf(phi.hi);
+  float r = __fadd_rn(__fsub_rn(phi.hi, n), phi.lo);
+  float s, c;
+  sincospif(2.0f * r, &s, &c);
+  return make_float2(c, s);
+}
+__device__ __forceinline__ float2 cis_cycles_d(double phi) {
+  double r = phi - rint(phi);
+  float s, c;
+  sincospif(2.0f * (float)r, &s, &c);
+  return make_float2(c, s);
+}
+
+// ------------------------------------------------------------------------------------
+// convolution kernel G (section 2, Eq. 3)
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ float kernel_eval(const KernelParams &k, float x) {
+  if (x < -k.half || x > k.half) return 0.0f;
+  if (k.kind == WST_KERNEL_GAUSS) return expf(-x * x * k.inv2s2);
+  if (k.kind == WST_KERNEL_ES) {
+    float z = x * k.two_over_w;
+    return expf(k.beta * (sqrtf(fmaxf(0.0f, 1.0f - z * z)) - 1.0f));
+  }
+  float pos = (x + k.half) * k.table_scale;
+  int i = (int)floorf(pos);
+  i = max(0, min(i, k.table_len - 2));
+  float f = pos - (float)i;
+  return fmaf(f, __ldg(k.table + i + 1) - __ldg(k.table + i), __ldg(k.table + i));
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+}  // namespace wst
+
+// ------------------------------------------------------------------------------------
+// host-side launchers (defined in the k_*.cu files)
+// ------------------------------------------------------------------------------------
+namespace wst {
+
+KernelParams kernel_params(const wst_plan_s *p);
+
+// k_tables.cu
+cudaError_t build_tables(wst_plan_s *p);
+cudaError_t build_correction(wst_plan_s *p);
+cudaError_t build_plane_centres(wst_plan_s *p);
+
+// k_sort.cu
+cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
+                              const float2 *vis, const float *weight);
+cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, int64_t n_bound);
+int64_t scan_tmp_words(int64_t n);
+
+// k_grid.cu
+cudaError_t grid_planes(wst_plan_s *p, int p0, int p1, float2 *out, bool checker);
+cudaError_t degrid_planes(wst_plan_s *p, int p0, int p1, const float2 *planes, float2 *dvis);
+cudaError_t kernel_grad_planes(wst_plan_s *p, int p0, int p1, const float2 *planes, float *dtab);
+
+// k_fft.cu
+cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool presign,
+                     bool postsign);
+cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first);
+// forward: accumulate planes [p0,p1) (stored at planes[0..]) into image (+comp)
+cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1,
+                                  float2 *image, float2 *comp, bool kahan, bool correct,
+                                  bool staged_add);
+// adjoint: planes [p0,p1) from the image tile: sign * conj(screen) * corr * dimage, DFT(-1)
+cudaError_t fft_cols_bh_from_image(wst_plan_s *p, const float2 *dimage, int p0, int p1,
+                                   float2 *planes, bool correct);
+cudaError_t correct_image(wst_plan_s *p, float2 *image);
+
+// k_dft.cu
+cudaError_t dft_pixels(int64_t n_vis, const float *u, const float *v, const float *w,
+                       const float2 *vis, const float *weight, int n, double fov, int64_t n_pix,
+                       const int32_t *pa, const int32_t *pb, float2 *out, cudaStream_t s);
+cudaError_t predict_points(int64_t n_vis, const float *u, const float *v, const float *w,
+                           int64_t n_src, const double *l, const double *m, const double *flux,
+                           float2 *out, cudaStream_t s);
+
+}  // namespace wst

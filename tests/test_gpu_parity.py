@@ -1,0 +1,259 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerance (the benchmark spec): max |D_gpu - D_oracle| <= 1e-5 * max |D_oracle| for images and
+planes computed in FP32; placement (plane, tap start) and counts are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleConfig
+from paper_2301_06061_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def wst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_06061_gb300 import build, wst as w
+
+    build.build()
+    w.load_library()
+    return w
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rel_err(gpu, ref):
+    ref = np.asarray(ref)
+    scale = np.abs(ref).max()
+    return float(np.abs(np.asarray(gpu, dtype=np.complex128) - ref).max() / max(scale, 1e-300))
+
+
+def make_case(n=256, fov=0.1, n_w=8, n_vis=3000, W=7, seed=0, radius=0.45, w_half=200.0):
+    rng = np.random.default_rng(seed)
+    u, v, w = synth.disk_uvw(n_vis, radius * n / fov, w_half, rng)
+    vis = synth.random_visibilities(n_vis, rng)
+    return u, v, w, vis
+
+
+def ocfg_for(cfg, w_min, w_max, table=None):
+    kern = {0: "gauss", 1: "es", 2: "table"}[cfg.kernel]
+    return OracleConfig(cfg.n, cfg.fov, cfg.n_w, w_min, w_max, cfg.support, kern, cfg.kparam,
+                        None if table is None else np.asarray(table, np.float64))
+
+
+def gpu_plan(wst, cfg, u, v, w, vis, weight=None, offsets=None, table=None):
+    plan = wst.Plan(cfg)
+    if table is not None:
+        plan.set_kernel_table(dev(np.asarray(table, np.float32)))
+    plan.set_vis(dev(u), dev(v), dev(w), dev(vis), None if weight is None else dev(weight), offsets)
+    return plan
+
+
+# ------------------------------------------------------------------------------------------
+# K-S: placement is bit-exact
+# ------------------------------------------------------------------------------------------
+
+def test_vis_cells_bit_exact(wst):
+    u, v, w, vis = make_case(n=256, n_vis=20000, radius=0.55, w_half=230.0)  # some dropped
+    u[:5] = np.nan
+    vis[5:8] = np.nan
+    cfg = wst.Config(n=256, fov=0.1, n_w=8, w_min=-200.0, w_max=200.0)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    k = torch.empty(u.size, dtype=torch.int32, device="cuda")
+    i0 = torch.empty_like(k)
+    j0 = torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    ko, io, jo, st = oracle.locate(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis)
+    np.testing.assert_array_equal(k.cpu().numpy(), ko)
+    np.testing.assert_array_equal(i0.cpu().numpy(), io)
+    np.testing.assert_array_equal(j0.cpu().numpy(), jo)
+    s = plan.stats()
+    assert s["n_kept"] == int((st == 0).sum())
+    assert s["n_dropped"] == int((st == 1).sum()) > 0
+    assert s["n_nonfinite"] == int((st == 2).sum()) == 8
+
+
+def test_w_range_from_data(wst):
+    u, v, w, vis = make_case(n=128, n_vis=5000)
+    cfg = wst.Config(n=128, fov=0.1, n_w=5)  # w_min == w_max: from the data
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    lo, hi = oracle.resolve_w_range(w, 0.0, 0.0)
+    s = plan.stats()
+    assert s["w_min"] == lo and s["w_max"] == hi
+    k = torch.empty(u.size, dtype=torch.int32, device="cuda")
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    ko, _, _, _ = oracle.locate(ocfg_for(cfg, lo, hi), u, v, w, vis)
+    np.testing.assert_array_equal(k.cpu().numpy(), ko)
+
+
+# ------------------------------------------------------------------------------------------
+# K-G: gridded planes
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,W", [(64, 7), (256, 7), (256, 8), (512, 5)])
+def test_grid_planes(wst, n, W):
+    u, v, w, vis = make_case(n=n, n_vis=4000, seed=n + W)
+    wt = np.random.default_rng(1).uniform(0.5, 2.0, u.size).astype(np.float32)
+    cfg = wst.Config(n=n, fov=0.1, n_w=6, w_min=-200.0, w_max=200.0, support=W,
+                     kparam=wst.DEFAULT_SIGMA.get(W, 0.8))
+    plan = gpu_plan(wst, cfg, u, v, w, vis, weight=wt)
+    g = torch.empty((6, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_grid(plan.handle, 0, 6, g)
+    ref = oracle.grid(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis, wt)
+    assert rel_err(g.cpu().numpy(), ref) < TOL
+
+
+def test_grid_dense_tile_collisions(wst):
+    """Thousands of visibilities in one tile: shared-memory accumulation under contention."""
+    rng = np.random.default_rng(3)
+    n, fov = 256, 0.1
+    u = rng.normal(0.0, 30.0, 20000).astype(np.float32)
+    v = rng.normal(0.0, 30.0, 20000).astype(np.float32)
+    w = rng.uniform(-10, 10, 20000).astype(np.float32)
+    vis = synth.random_visibilities(20000, rng)
+    cfg = wst.Config(n=n, fov=fov, n_w=2, w_min=-10.0, w_max=10.0)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    g = torch.empty((2, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_grid(plan.handle, 0, 2, g)
+    ref = oracle.grid(ocfg_for(cfg, -10.0, 10.0), u, v, w, vis)
+    assert rel_err(g.cpu().numpy(), ref) < TOL
+
+
+# ------------------------------------------------------------------------------------------
+# K-F + K-P: transform, screen and plane sum; full image
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [64, 128, 256, 512, 1024, 2048])
+def test_fft_correct_staged(wst, n):
+    u, v, w, vis = make_case(n=n, n_vis=3000, seed=n)
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    g = torch.empty((4, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_grid(plan.handle, 0, 4, g)
+    img = torch.zeros((1, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_fft_correct(plan.handle, 0, 2, g[0:2].contiguous(), img)
+    wst.wst_fft_correct(plan.handle, 2, 4, g[2:4].contiguous(), img)
+    ref = oracle.image(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis, correct=False)
+    assert rel_err(img[0].cpu().numpy(), ref) < TOL
+    wst.wst_correct(plan.handle, img)
+    ref_c = oracle.image(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis, correct=True)
+    assert rel_err(img[0].cpu().numpy(), ref_c) < TOL
+
+
+@pytest.mark.parametrize("n,n_w,chunk,flags", [
+    (256, 8, 0, 1), (256, 8, 3, 1), (256, 8, 3, 0), (512, 5, 2, 1), (1024, 4, 0, 3), (64, 1, 0, 1),
+    (4096, 2, 1, 1),
+])
+def test_image_end_to_end(wst, n, n_w, chunk, flags):
+    u, v, w, vis = make_case(n=n, n_vis=4000, seed=7 * n + n_w)
+    cfg = wst.Config(n=n, fov=0.1, n_w=n_w, w_min=-200.0, w_max=200.0, flags=flags, planes_per_chunk=chunk)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    img = plan.image()
+    ref = oracle.image(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis)
+    assert rel_err(img[0].cpu().numpy(), ref) < TOL
+    assert plan.stats()["n_chunks"] == (-(-n_w // chunk) if chunk else 1)
+
+
+@pytest.mark.parametrize("kernel,W,param", [("es", 8, 2.3 * 8), ("gauss", 8, 0.925), ("table", 8, None)])
+def test_image_kernels(wst, kernel, W, param):
+    n = 256
+    u, v, w, vis = make_case(n=n, n_vis=3000, seed=11)
+    table = None
+    if kernel == "table":
+        x = np.linspace(-W / 2, W / 2, W * 64 + 1)
+        table = np.exp(-x**2 / (2 * 0.925**2)) * (1 + 0.1 * np.cos(3 * x))
+    kid = {"gauss": 0, "es": 1, "table": 2}[kernel]
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0, support=W, kernel=kid,
+                     kparam=param or 0.0, ktable_len=0 if table is None else table.size)
+    plan = gpu_plan(wst, cfg, u, v, w, vis, table=table)
+    img = plan.image()
+    t32 = None if table is None else table.astype(np.float32)
+    ref = oracle.image(ocfg_for(cfg, -200.0, 200.0, t32), u, v, w, vis)
+    assert rel_err(img[0].cpu().numpy(), ref) < TOL
+
+
+def test_image_weights_and_nonfinite(wst):
+    n = 256
+    u, v, w, vis = make_case(n=n, n_vis=3000, seed=5)
+    wt = np.random.default_rng(9).uniform(0.0, 3.0, u.size).astype(np.float32)
+    wt[10] = np.inf
+    w[11] = np.nan
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0)
+    plan = gpu_plan(wst, cfg, u, v, w, vis, weight=wt)
+    img = plan.image()
+    ref = oracle.image(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis, wt)
+    assert rel_err(img[0].cpu().numpy(), ref) < TOL
+    assert plan.stats()["n_nonfinite"] == 2
+
+
+def test_image_empty_and_all_dropped(wst):
+    n = 128
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-1.0, w_max=1.0)
+    plan = wst.Plan(cfg)
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    plan.set_vis(e, e, e, torch.empty(0, dtype=torch.complex64, device="cuda"))
+    img = plan.image()
+    assert torch.count_nonzero(img).item() == 0
+    far = np.full(100, 5000.0, np.float32)
+    plan.set_vis(dev(far), dev(far), dev(np.zeros(100, np.float32)), dev(np.ones(100, np.complex64)))
+    img = plan.image()
+    assert torch.count_nonzero(img).item() == 0
+    assert plan.stats()["n_dropped"] == 100
+
+
+def test_single_visibility_flat_image(wst):
+    n = 256
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-30.0, w_max=30.0)
+    plan = gpu_plan(wst, cfg, np.zeros(1, np.float32), np.zeros(1, np.float32), np.zeros(1, np.float32),
+                    np.ones(1, np.complex64))
+    img = plan.image()[0].cpu().numpy()
+    ref = oracle.image(ocfg_for(cfg, -30.0, 30.0), [0.0], [0.0], [0.0], np.ones(1, np.complex64))
+    assert rel_err(img, ref) < TOL
+    c = slice(n // 4, 3 * n // 4)
+    assert np.abs(img[c, c] - 1).max() < 3e-3
+
+
+def test_batched_images(wst):
+    n, n_w = 256, 4
+    counts = [500, 0, 2500, 1200]
+    rng = np.random.default_rng(17)
+    us, vs, ws, viss = [], [], [], []
+    for c in counts:
+        u, v, w = synth.disk_uvw(c, 0.45 * n / 0.1, 150.0, rng)
+        us.append(u); vs.append(v); ws.append(w); viss.append(synth.random_visibilities(c, rng))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    U, V, Wv, VIS = (np.concatenate(x) for x in (us, vs, ws, viss))
+    cfg = wst.Config(n=n, fov=0.1, n_w=n_w, batch=len(counts), planes_per_chunk=3)
+    plan = gpu_plan(wst, cfg, U, V, Wv, VIS, offsets=off)
+    img = plan.image().cpu().numpy()
+    for b, c in enumerate(counts):
+        if c == 0:
+            assert np.all(img[b] == 0)
+            continue
+        lo, hi = oracle.resolve_w_range(ws[b], 0.0, 0.0)
+        ref = oracle.image(ocfg_for(cfg, lo, hi), us[b], vs[b], ws[b], viss[b])
+        assert rel_err(img[b], ref) < TOL, b
+
+
+def test_wide_field_outside_sphere_zero(wst):
+    n = 128
+    cfg = wst.Config(n=n, fov=2.4, n_w=2, w_min=-5.0, w_max=5.0)
+    u, v, w, vis = make_case(n=n, fov=2.4, n_vis=500, w_half=5.0)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    img = plan.image()[0].cpu().numpy()
+    ref = oracle.image(ocfg_for(cfg, -5.0, 5.0), u, v, w, vis)
+    assert rel_err(img, ref) < TOL
+    assert np.all(img[ref == 0] == 0)
