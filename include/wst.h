@@ -19,7 +19,8 @@
  *   - A visibility at x = N/2 + u FoV (computed in FP64) touches the W cells
  *     i0 = ceil(x - W/2) ... i0 + W - 1 with weight G(i - x) (same along v).
  *     A visibility whose footprint leaves [0, N) on either axis is dropped and
- *     counted; one with a non-finite u, v, w, value or weight is counted apart.
+ *     counted; one with a non-finite u, v, w, value or weight is counted apart
+ *     (as non-finite, whatever its footprint).
  *   - Planes are cell-centred on [w_min, w_max]: k = clamp(floor((w - w_min) *
  *     (N_w / (w_max - w_min))), 0, N_w - 1), centre w_k = w_min + (k + 1/2) dw.
  *   - The image is the unnormalised dirty image

@@ -202,7 +202,8 @@ int64_t wo_locate(const wo_config *c, int64_t n_vis, const float *u, const float
     int32_t k = -1, i0 = -1, j0 = -1;
     double x, y;
     int st = locate_one(c, u[j], v[j], w[j], &k, &i0, &j0, &x, &y);
-    if (st == WO_KEPT && !vis_finite(vis, weight, j)) st = WO_NONFINITE;
+    /* a non-finite input of any kind is counted as such, before the footprint test */
+    if (!vis_finite(vis, weight, j)) st = WO_NONFINITE;
     if (st != WO_KEPT) k = i0 = j0 = -1;
     else ++kept;
     if (k_out) k_out[j] = k;
