@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the w-stacking hot path: Mvis/s of the end-to-end image.
+
+Default workload (one GPU): 16384^2 image, 32 w-planes, 1e8 visibilities from
+300-station 8 h earth-rotation tracks over 64 channels (120-168 MHz), Gaussian
+kernel W=7.  One step = bucket sort (wst_plan_set_vis) + gridding, per-plane 2D
+FFT, phase screen, plane sum and grid correction (wst_image), inputs resident in
+HBM.  Prints one JSON line (see the keys below).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large|array|batched] [--chunk P]
+
+--impl reference times the FP64 CPU oracle (the only CPU program of this method
+here) on a bounded sample of the same workload.  Under torchrun every rank images
+its own copy of the workload (replicas, weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mvis/s end-to-end w-stacking image (16384², 32 planes) + max err vs FP64 DFT"
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    "large": "16384^2 image, 32 w-planes, 1e8 visibilities (300 stations, 8 h tracks at dec +45, "
+             "64 channels 120-168 MHz, 35 dumps), FoV 0.5 rad, Gaussian W=7 sigma=0.875",
+    "array": "4096^2 image, 32 w-planes, 4.08e6 visibilities (60 stations, 144 dumps, 16 channels), "
+             "FoV 0.2 rad, Gaussian W=7",
+    "batched": "64 channel images of 2048^2, 16 w-planes each, 1e5-2e6 visibilities per image (log-uniform), "
+               "FoV 0.09 rad, Gaussian W=7",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--chunk", type=int, default=0, help="planes per chunk (0 = all planes resident)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dft-pixels", type=int, default=64)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# workloads (seeded, synthetic; see paper_2301_06061_gb300/synth.py)
+# ------------------------------------------------------------------------------------------
+
+def make_workload(name: str, rank: int):
+    from paper_2301_06061_gb300 import synth
+
+    if name == "large":
+        work = synth.large(seed_extra=rank)
+    elif name == "array":
+        work = synth.array(seed_extra=rank)
+    else:
+        work = synth.batched(seed_extra=rank)
+    # visibility values do not change any kernel's work: seeded complex Gaussian values
+    vis = synth.random_visibilities(work.n_vis, synth.rng_for(3, 7 + rank))
+    return work, vis
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ------------------------------------------------------------------------------------------
+
+def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept: int, n_vis: int) -> float:
+    """Algorithmic DRAM bytes of one launch of a stage (averaged over the chunks)."""
+    S = 8.0 * n * n
+    per_chunk_planes = planes / chunks
+    if stage == "sort":  # read u, v, w, V (20 B) and write the record and index (20 B)
+        return 40.0 * n_vis
+    if stage == "grid":  # write every plane cell once, read the records once
+        return per_chunk_planes * S + 16.0 * n_kept / chunks
+    if stage in ("rows", "cols_a"):  # read + write each plane
+        return 2.0 * per_chunk_planes * S
+    if stage == "cols_b":  # read each plane, write the images once
+        return per_chunk_planes * S + batch * S / chunks
+    raise ValueError(stage)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2301_06061_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2301_06061_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_stage: str, workload: str, launch_scale: float):
+    """DRAM bytes per launch from the committed ncu summary, if it matches these sources."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m_hash or m_hash.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"{kernel_stage}_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) * launch_scale if m else None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample(work, vis, plane: int):
+    """One w-plane of the workload with its visibilities, as an n_w = 1 oracle problem."""
+    import oracle
+
+    lo, hi = oracle.resolve_w_range(work.w, work.w_min, work.w_max) if work.batch_offsets is None else (0, 0)
+    full = oracle.OracleConfig(work.n, work.fov, work.n_w, lo, hi, work.support, "gauss", 0.875)
+    k, _, _, st = oracle.locate(full, work.u, work.v, work.w, vis)
+    sel = np.nonzero((st == 0) & (k == plane))[0]
+    dw = (hi - lo) / work.n_w
+    cfg = oracle.OracleConfig(work.n, work.fov, 1, lo + plane * dw, lo + (plane + 1) * dw, work.support,
+                              "gauss", 0.875)
+    return cfg, work.u[sel], work.v[sel], work.w[sel], vis[sel]
+
+
+def time_oracle_sample(work, vis, repeats: int = 1):
+    """Seconds per full job, extrapolated from one plane of the single-image workloads."""
+    import oracle
+
+    plane = work.n_w // 2
+    cfg, u, v, w, vv = oracle_sample(work, vis, plane)
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.image(cfg, u, v, w, vv)
+        times.append(time.perf_counter() - t0)
+    t_plane = statistics.median(times)
+    job_s = t_plane * work.n_w  # the job is n_w such planes (plus their share of visibilities)
+    sample = (f"w-plane {plane} of {work.n_w} ({u.size} of {work.n_vis} visibilities, {work.n}^2 FP64 grid, "
+              f"FFT, screen, correction); time x {work.n_w} planes")
+    return job_s, sample, oracle.num_threads()
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_2301_06061_gb300 import build, wst
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build.build()
+    work, vis_np = make_workload(args.workload, rank)
+    n_vis = work.n_vis
+    batch = 1 if work.batch_offsets is None else len(work.batch_offsets) - 1
+    cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
+                     support=work.support, kparam=wst.DEFAULT_SIGMA[work.support],
+                     flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING, planes_per_chunk=args.chunk, batch=batch)
+    dev = torch.device("cuda", local_rank)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_u, h_v, h_w, h_vis = pin(work.u), pin(work.v), pin(work.w), pin(vis_np)
+    d_u, d_v, d_w, d_vis = (t.to(dev) for t in (h_u, h_v, h_w, h_vis))
+    offsets = None if work.batch_offsets is None else [int(x) for x in work.batch_offsets]
+    plan = wst.Plan(cfg, device=dev)
+    img = torch.empty((batch, work.n, work.n), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.set_vis(d_u, d_v, d_w, d_vis, None, offsets)
+        plan.image(out=img)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.stats()  # drop warm-up timings
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    st = plan.stats()
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n_vis / (ms_step * 1e-3) / 1e6
+
+    # stage times inside the timed region (CUDA events on the plan's stream)
+    stages = {"sort": st["ms_sort"], "grid": st["ms_grid"], "rows": st["ms_rows"], "cols_a": st["ms_cols_a"],
+              "cols_b": st["ms_cols_b"]}
+    launches_per_stage = {"sort": 1, "grid": st["n_chunks"], "rows": st["n_chunks"], "cols_a": st["n_chunks"],
+                          "cols_b": st["n_chunks"]}
+    dom = max(stages, key=stages.get)
+    per_launch_ms = stages[dom] / (args.steps * launches_per_stage[dom])
+    planes = batch * work.n_w
+    bytes_launch = stage_bytes(dom, work.n, planes, st["n_chunks"], batch, st["n_kept"], n_vis)
+    peak, peak_src = load_peaks()
+    achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    kernel_names = {"sort": "k_keys+k_scan+k_scatter", "grid": "k_grid_tiles", "rows": "k_rows",
+                    "cols_a": "k_cols_a", "cols_b": "k_cols_b_acc"}
+    roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic(dom, args.workload, 1.0),
+                "bytes_per_launch": bytes_launch, "ms_per_launch": round(per_launch_ms, 4),
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stages.items()},
+                "stage_frac_of_hbm": {k: round(stage_bytes(k, work.n, planes, st["n_chunks"], batch, st["n_kept"],
+                                                           n_vis) * launches_per_stage[k] /
+                                               (v / args.steps * 1e-3) / 1e9 / peak, 4)
+                                      for k, v in stages.items() if v > 0}}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_img = torch.empty((batch, work.n, work.n), dtype=torch.complex64).pin_memory()
+
+        def e2e_step():
+            d_u.copy_(h_u, non_blocking=True)
+            d_v.copy_(h_v, non_blocking=True)
+            d_w.copy_(h_w, non_blocking=True)
+            d_vis.copy_(h_vis, non_blocking=True)
+            step()
+            h_img.copy_(img, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        n_e2e = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1) / n_e2e
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": round(world * n_vis / (e2e_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+               "h2d_bytes_per_step": int(20 * n_vis), "d2h_bytes_per_step": int(8 * batch * work.n * work.n),
+               "ms_per_step": round(e2e_ms, 3)}
+        plan.stats()
+
+    # accuracy: the image against the direct transform at seeded pixels (GPU judge, float-float phases)
+    acc = None
+    if args.dft_pixels > 0 and batch == 1:
+        rng = np.random.default_rng(20230106)
+        q = args.dft_pixels
+        n = work.n
+        pa = np.concatenate([rng.integers(3 * n // 8, 5 * n // 8, q // 2), rng.integers(0, n, q - q // 2)])
+        pb = np.concatenate([rng.integers(3 * n // 8, 5 * n // 8, q // 2), rng.integers(0, n, q - q // 2)])
+        d_pa = torch.from_numpy(pa.astype(np.int32)).to(dev)
+        d_pb = torch.from_numpy(pb.astype(np.int32)).to(dev)
+        dft = torch.empty(q, dtype=torch.complex64, device=dev)
+        wst.wst_dft(d_u, d_v, d_w, d_vis, n, work.fov, d_pa, d_pb, dft)
+        got = img[0][d_pb.long(), d_pa.long()]
+        err = (got - dft).abs()
+        peak_d = dft.abs().max().item()
+        acc = {"max_err_vs_dft_rel_peak": float(err.max().item() / peak_d),
+               "central_quarter_max_err_rel_peak": float(err[: q // 2].max().item() / peak_d),
+               "pixels": q, "judge": "wst_dft (GPU direct transform, float-float phases)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and batch == 1:
+        job_s, sample, cores = time_oracle_sample(work, vis_np)
+        cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mvis/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
+                       "n_vis": n_vis, "batch": batch, "planes_per_chunk": args.chunk or planes,
+                       "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
+                       "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(st["n_launches"]) * args.steps, "accuracy": acc,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    work, vis_np = make_workload(args.workload, 0)
+    if work.batch_offsets is not None:
+        print(json.dumps({"impl": "reference", "unavailable": "batched workload: the CPU oracle is timed on "
+                          "single-image workloads only"}))
+        return
+    import oracle
+
+    oracle.build()
+    times = []
+    sample = cores = None
+    for i in range(args.warmup + args.steps):
+        job_s, sample, cores = time_oracle_sample(work, vis_np)
+        if i >= args.warmup:
+            times.append(job_s)
+    job_s = statistics.mean(times)
+    value = work.n_vis / job_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mvis/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(job_s * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
+                       "n_vis": work.n_vis},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Mvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

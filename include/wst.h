@@ -97,9 +97,13 @@ typedef struct wst_stats {
   int64_t n_dropped;   /* footprint outside the grid                                   */
   int64_t n_nonfinite; /* non-finite u, v, w, value or weight                          */
   double w_min, w_max; /* plane range of image 0                                       */
-  float ms_sort, ms_grid, ms_fft, ms_correct, ms_total; /* last wst_image (TIMING flag) */
+  /* WST_FLAG_TIMING: CUDA-event times (ms) per stage, summed over every
+   * wst_plan_set_vis (sort) and wst_image call since the previous wst_get_stats;
+   * ms_total = grid + rows + cols_a + cols_b */
+  float ms_sort, ms_grid, ms_rows, ms_cols_a, ms_cols_b, ms_total;
   int32_t device_error; /* 0, or a WST_ERR_* raised on the device                       */
-  int32_t n_chunks;     /* plane chunks used by wst_image                               */
+  int32_t n_chunks;     /* plane chunks used by the last wst_image                      */
+  int64_t n_launches;   /* kernels launched by the last set_vis + wst_image             */
 } wst_stats;
 
 typedef struct wst_plan_s *wst_plan;
@@ -114,7 +118,7 @@ const char *wst_status_string(wst_status s);
  * Create a plan for one imaging geometry (section 2: the mesh N_u x N_v x N_w and
  * the kernel of Eq. 3).  `cuda_stream` is a cudaStream_t (NULL = legacy default
  * stream).  Builds, on the device, the FFT twiddles, the grid-correction table
- * 1/Ghat(nu) (Gauss-Legendre quadrature in FP64) and the l^2 terms of the phase
+ * 1/Ghat(nu) (composite Simpson quadrature in FP64) and the l^2 terms of the phase
  * screen.  For WST_KERNEL_TABLE the correction is built by wst_plan_set_kernel_table.
  * Errors: INVALID_ARG (bad config), UNSUPPORTED, OOM, CUDA.  *out is NULL on error.
  */
@@ -140,8 +144,8 @@ wst_status wst_plan_set_workspace(wst_plan plan, void *device_ptr, size_t bytes)
 
 /*
  * WST_KERNEL_TABLE only: copy `ktable_len` FP32 samples (device pointer) of G on
- * [-W/2, W/2] into the plan and rebuild 1/Ghat on the device (the integral of a
- * piecewise-linear function times cos, in closed form per interval, FP64).
+ * [-W/2, W/2] into the plan and rebuild 1/Ghat on the device (Simpson's rule on
+ * every table interval in FP64, so that the interpolation kinks are panel ends).
  */
 wst_status wst_plan_set_kernel_table(wst_plan plan, const float *table_dev);
 

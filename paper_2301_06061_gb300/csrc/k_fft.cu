@@ -589,6 +589,7 @@ static cudaError_t rows_dispatch(int n, float2 *planes, int nplanes, const float
 
 cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool presign, bool postsign) {
   if (nplanes <= 0) return cudaSuccess;
+  p->launches += 1;
   if (dir > 0 && !presign && !postsign) return rows_dispatch<1, false, false>(p->n, planes, nplanes, p->tw, p->stream);
   if (dir > 0 && presign && !postsign) return rows_dispatch<1, true, false>(p->n, planes, nplanes, p->tw, p->stream);
   if (dir < 0 && !presign && postsign) return rows_dispatch<-1, false, true>(p->n, planes, nplanes, p->tw, p->stream);
@@ -616,6 +617,7 @@ static cudaError_t cols_a_dispatch(wst_plan_s *p, float2 *planes, int nplanes) {
 
 cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first) {
   if (nplanes <= 0) return cudaSuccess;
+  p->launches += 1;
   if (dir > 0 && !twiddle_first) return cols_a_dispatch<1, false>(p, planes, nplanes);
   if (dir < 0 && twiddle_first) return cols_a_dispatch<-1, true>(p, planes, nplanes);
   return cudaErrorInvalidValue;
@@ -644,6 +646,7 @@ static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, in
 cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                   float2 *comp, bool kahan, bool correct, bool staged_add) {
   if (p1 <= p0) return cudaSuccess;
+  p->launches += 1;
   int flags = 0;
   if (correct) flags |= ACC_CORRECT;
   if (kahan) flags |= ACC_KAHAN;
@@ -670,6 +673,7 @@ static cudaError_t launch_cols_bh(wst_plan_s *p, const float2 *dimage, int p0, i
 cudaError_t fft_cols_bh_from_image(wst_plan_s *p, const float2 *dimage, int p0, int p1, float2 *planes,
                                    bool correct) {
   if (p1 <= p0) return cudaSuccess;
+  p->launches += 1;
   switch (p->fa) {
     case 8: return launch_cols_bh<8>(p, dimage, p0, p1, planes, correct);
     case 16: return launch_cols_bh<16>(p, dimage, p0, p1, planes, correct);
@@ -685,6 +689,7 @@ cudaError_t correct_image(wst_plan_s *p, float2 *image) {
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_correct<<<(unsigned)blocks, 256, 0, p->stream>>>(image, p->corr, p->n, total);
+  p->launches += 1;
   return cudaGetLastError();
 }
 

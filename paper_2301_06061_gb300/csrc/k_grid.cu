@@ -144,6 +144,7 @@ cudaError_t grid_planes(wst_plan_s *p, int p0, int p1, float2 *out, bool checker
   dim3 grd(p->tiles * p->tiles, np);
   k_grid_tiles<<<grd, kGridThreads, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, p->tiles,
                                                        p->n, kernel_params(p), out, checker ? 1 : 0);
+  p->launches += 1;
   return cudaGetLastError();
 }
 
@@ -273,6 +274,7 @@ cudaError_t degrid_planes(wst_plan_s *p, int p0, int p1, const float2 *planes, f
   k_degrid_tiles<false><<<grd, kGridThreads, smem, p->stream>>>(
       p->W_.records, p->W_.offsets, p->W_.perm, p->has_weight ? p->W_.rweight : nullptr, p0,
       p->tiles, p->n, kernel_params(p), planes, dvis, nullptr);
+  p->launches += 1;
   return cudaGetLastError();
 }
 
@@ -291,6 +293,7 @@ cudaError_t kernel_grad_planes(wst_plan_s *p, int p0, int p1, const float2 *plan
   k_degrid_tiles<true><<<grd, kGridThreads, smem, p->stream>>>(
       p->W_.records, p->W_.offsets, p->W_.perm, nullptr, p0, p->tiles, p->n, kernel_params(p),
       planes, nullptr, dtab);
+  p->launches += 1;
   return cudaGetLastError();
 }
 

@@ -211,16 +211,19 @@ int64_t scan_tmp_words(int64_t n) {
   return words + 64;
 }
 
-static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cudaStream_t s) {
+static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cudaStream_t s,
+                                  int64_t &launches) {
   const int64_t nb = scan_blocks(n);
   if (nb <= 1) {
     k_scan_apply<<<1, kScanThreads, 0, s>>>(data, n, nullptr);
+    launches += 1;
     return cudaGetLastError();
   }
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, tmp);
-  cudaError_t e = scan_exclusive(tmp, nb, tmp + nb + 64, s);
+  cudaError_t e = scan_exclusive(tmp, nb, tmp + nb + 64, s, launches);
   if (e != cudaSuccess) return e;
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(data, n, tmp);
+  launches += 2;
   return cudaGetLastError();
 }
 
@@ -268,7 +271,10 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   }
   const int64_t avg = p->n_vis / p->batch + 1;
   dim3 grd(grid_for(avg, 256, 4096), p->batch);
-  if (p->cfg.w_min == p->cfg.w_max) k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax);
+  if (p->cfg.w_min == p->cfg.w_max) {
+    k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax);
+    p->launches += 1;
+  }
   if ((e = build_plane_centres(p))) return e;
   SortGeom g;
   g.n = p->n;
@@ -280,11 +286,13 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   g.fov = p->cfg.fov;
   k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, g, ws.offsets,
                                ws.keyinfo, ws.counters);
+  p->launches += 1;
   if ((e = cudaGetLastError())) return e;
-  if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s))) return e;
+  if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(
       vis, weight, ws.keyinfo, ws.offsets, p->n_vis, ws.records, ws.perm,
       weight ? ws.rweight : nullptr);
+  p->launches += 1;
   return cudaGetLastError();
 }
 
@@ -326,6 +334,7 @@ cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, i
     k_vis_cells<<<grid_for(n_bound, 256, 152 * 16), 256, 0, s>>>(
         p->W_.records, p->W_.perm, p->W_.offsets, p->n_buckets, n_bound, p->tiles, p->n_w, plane,
         i0, j0);
+  p->launches += 1;
   return cudaGetLastError();
 }
 

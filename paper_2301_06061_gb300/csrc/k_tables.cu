@@ -90,12 +90,14 @@ cudaError_t build_tables(wst_plan_s *p) {
   const int n = p->n;
   k_twiddles<<<(n + 255) / 256, 256, 0, p->stream>>>(p->tw, n);
   k_l2<<<(n + 255) / 256, 256, 0, p->stream>>>(p->l2ff, p->l2d, n, p->cfg.fov / (double)n);
+  p->launches += 2;
   return cudaGetLastError();
 }
 
 cudaError_t build_correction(wst_plan_s *p) {
   k_correction<<<p->n, 256, 0, p->stream>>>(p->corr, p->n, p->cfg.kernel, p->W, p->cfg.kparam,
                                              p->ktable, p->cfg.ktable_len);
+  p->launches += 1;
   return cudaGetLastError();
 }
 
@@ -139,6 +141,7 @@ cudaError_t build_plane_centres(wst_plan_s *p) {
   k_plane_centres<<<(p->batch + 63) / 64, 64, 0, p->stream>>>(
       p->wrange, p->wcentre, p->wcentre_d, p->W_.wminmax, p->batch, p->n_w, p->cfg.w_min,
       p->cfg.w_max, from_data ? 1 : 0);
+  p->launches += 1;
   return cudaGetLastError();
 }
 

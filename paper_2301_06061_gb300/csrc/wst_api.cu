@@ -92,8 +92,32 @@ void destroy_tables(wst_plan_s *p) {
   cudaFree(p->wcentre);
   cudaFree(p->wcentre_d);
   cudaFree(p->batch_off);
-  for (auto &e : p->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto *l : {&p->ev_sort, &p->ev_img})
+    for (auto e : l->ev) cudaEventDestroy(e);
+}
+
+// stage ids of the timing event pairs
+enum { ST_SORT = 0, ST_GRID = 1, ST_ROWS = 2, ST_COLS_A = 3, ST_COLS_B = 4 };
+
+cudaError_t time_begin(wst_plan_s *p, wst_plan_s::EventList &l, int stage) {
+  if (!p->timing) return cudaSuccess;
+  const size_t need = 2 * (size_t)(l.used + 1);
+  while (l.ev.size() < need) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    l.ev.push_back(e);
+  }
+  if (l.stage.size() < (size_t)l.used + 1) l.stage.resize(l.used + 1);
+  l.stage[l.used] = stage;
+  return cudaEventRecord(l.ev[2 * l.used], p->stream);
+}
+
+cudaError_t time_end(wst_plan_s *p, wst_plan_s::EventList &l) {
+  if (!p->timing) return cudaSuccess;
+  cudaError_t r = cudaEventRecord(l.ev[2 * l.used + 1], p->stream);
+  ++l.used;
+  return r;
 }
 
 }  // namespace
@@ -170,9 +194,6 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   ALLOC(p->batch_off, c.batch + 1);
   if (c.kernel == WST_KERNEL_TABLE) ALLOC(p->ktable, c.ktable_len);
 #undef ALLOC
-  if (e == cudaSuccess && p->timing)
-    for (auto &ev : p->ev)
-      if (e == cudaSuccess) e = cudaEventCreate(&ev);
   if (e != cudaSuccess) {
     destroy_tables(p);
     delete p;
@@ -261,7 +282,9 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.wminmax = (uint32_t *)(p->ws + L.wminmax);
   W.comp = (p->chunk < p->n_planes) ? (float2 *)(p->ws + L.comp) : nullptr;
   W.bytes = L.total;
+  p->launches = 0;
   for (int i0 = 0; i0 <= p->batch; i0 += 64) {
+    ++p->launches;
     OffsetsArg a;
     const int cnt = (p->batch + 1 - i0) < 64 ? (p->batch + 1 - i0) : 64;
     for (int i = 0; i < cnt; ++i) a.v[i] = off[i0 + i];
@@ -270,9 +293,10 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   WST_CUDA(p, cudaGetLastError(), "batch offsets");
   p->n_vis = n_vis;
   p->has_weight = weight != nullptr;
-  if (p->timing) WST_CUDA(p, cudaEventRecord(p->ev[0], p->stream), "event");
+  WST_CUDA(p, time_begin(p, p->ev_sort, ST_SORT), "event");
   WST_CUDA(p, sort_visibilities(p, u, v, w, (const float2 *)vis, weight), "sort");
-  if (p->timing) WST_CUDA(p, cudaEventRecord(p->ev[1], p->stream), "event");
+  WST_CUDA(p, time_end(p, p->ev_sort), "event");
+  p->launches_sort = p->launches;
   p->vis_set = true;
   return WST_OK;
 }
@@ -324,21 +348,24 @@ wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
   float2 *img = (float2 *)image_out;
   float2 *planes = p->W_.planes;
   p->n_chunks = 0;
-  if (p->timing) WST_CUDA(p, cudaEventRecord(p->ev[2], p->stream), "event");
+  p->launches = 0;
   for (int p0 = 0; p0 < p->n_planes; p0 += p->chunk) {
     const int p1 = (p0 + p->chunk < p->n_planes) ? p0 + p->chunk : p->n_planes;
+    WST_CUDA(p, time_begin(p, p->ev_img, ST_GRID), "event");
     WST_CUDA(p, grid_planes(p, p0, p1, planes, true), "grid");
-    if (p->timing && p0 == 0) WST_CUDA(p, cudaEventRecord(p->ev[3], p->stream), "event");
+    WST_CUDA(p, time_end(p, p->ev_img), "event");
+    WST_CUDA(p, time_begin(p, p->ev_img, ST_ROWS), "event");
     WST_CUDA(p, fft_rows(p, planes, p1 - p0, +1, false, false), "rows");
+    WST_CUDA(p, time_end(p, p->ev_img), "event");
+    WST_CUDA(p, time_begin(p, p->ev_img, ST_COLS_A), "event");
     WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, +1, false), "cols A");
-    if (p->timing && p0 == 0) WST_CUDA(p, cudaEventRecord(p->ev[4], p->stream), "event");
+    WST_CUDA(p, time_end(p, p->ev_img), "event");
+    WST_CUDA(p, time_begin(p, p->ev_img, ST_COLS_B), "event");
     WST_CUDA(p, fft_cols_b_accumulate(p, planes, p0, p1, img, p->W_.comp, kahan, correct, false), "cols B");
+    WST_CUDA(p, time_end(p, p->ev_img), "event");
     ++p->n_chunks;
   }
-  if (p->timing) {
-    WST_CUDA(p, cudaEventRecord(p->ev[5], p->stream), "event");
-    p->ms_pending = true;
-  }
+  p->launches_image = p->launches;
   return WST_OK;
 }
 
@@ -406,19 +433,19 @@ wst_status wst_get_stats(wst_plan p, wst_stats *out) {
     out->w_min = wr[0];
     out->w_max = wr[3];
   }
-  if (p->timing && p->ms_pending) {
-    cudaEventElapsedTime(&p->ms[0], p->ev[0], p->ev[1]);  // sort (last set_vis)
-    cudaEventElapsedTime(&p->ms[1], p->ev[2], p->ev[3]);  // grid (first chunk)
-    cudaEventElapsedTime(&p->ms[2], p->ev[3], p->ev[4]);  // rows + cols A (first chunk)
-    cudaEventElapsedTime(&p->ms[3], p->ev[4], p->ev[5]);  // cols B + screen + rest
-    cudaEventElapsedTime(&p->ms[4], p->ev[2], p->ev[5]);  // image total
-    p->ms_pending = false;
+  if (p->timing) {  // sums since the previous wst_get_stats, then the lists restart
+    float *dst[5] = {&out->ms_sort, &out->ms_grid, &out->ms_rows, &out->ms_cols_a, &out->ms_cols_b};
+    for (auto *l : {&p->ev_sort, &p->ev_img}) {
+      for (int i = 0; i < l->used; ++i) {
+        float ms = 0.0f;
+        WST_CUDA(p, cudaEventElapsedTime(&ms, l->ev[2 * i], l->ev[2 * i + 1]), "event time");
+        *dst[l->stage[i]] += ms;
+      }
+      l->used = 0;
+    }
+    out->ms_total = out->ms_grid + out->ms_rows + out->ms_cols_a + out->ms_cols_b;
   }
-  out->ms_sort = p->ms[0];
-  out->ms_grid = p->ms[1];
-  out->ms_fft = p->ms[2];
-  out->ms_correct = p->ms[3];
-  out->ms_total = p->ms[4];
+  out->n_launches = p->launches_sort + p->launches_image;
   return out->device_error ? WST_ERR_TIMEOUT : WST_OK;
 }
 

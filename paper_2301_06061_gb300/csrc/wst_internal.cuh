@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "wst.h"
 
@@ -83,12 +84,17 @@ struct wst_plan_s {
   bool vis_set = false;
   bool has_weight = false;
   int64_t *batch_off = nullptr;  // device copy of batch offsets [batch+1]
-  // timing
-  cudaEvent_t ev[6] = {};
+  // timing: CUDA events recorded around each stage launch (WST_FLAG_TIMING)
+  struct EventList {
+    std::vector<cudaEvent_t> ev;  // pairs (2i, 2i+1)
+    std::vector<int> stage;       // stage id of pair i
+    int used = 0;
+  };
   bool timing = false;
-  float ms[5] = {0, 0, 0, 0, 0};
-  bool ms_pending = false;
+  EventList ev_sort, ev_img;
   int n_chunks = 0;
+  int64_t launches_sort = 0, launches_image = 0;
+  int64_t launches = 0;       // incremented by every launcher
   std::string last_error;
 };
 

@@ -68,11 +68,13 @@ class wst_stats(ctypes.Structure):
         ("w_max", ctypes.c_double),
         ("ms_sort", ctypes.c_float),
         ("ms_grid", ctypes.c_float),
-        ("ms_fft", ctypes.c_float),
-        ("ms_correct", ctypes.c_float),
+        ("ms_rows", ctypes.c_float),
+        ("ms_cols_a", ctypes.c_float),
+        ("ms_cols_b", ctypes.c_float),
         ("ms_total", ctypes.c_float),
         ("device_error", ctypes.c_int32),
         ("n_chunks", ctypes.c_int32),
+        ("n_launches", ctypes.c_int64),
     ]
 
 
