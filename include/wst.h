@@ -239,6 +239,44 @@ wst_status wst_predict_points(int64_t n_vis, const float *u, const float *v, con
                               int64_t n_src, const double *l, const double *m, const double *flux,
                               void *out, void *cuda_stream);
 
+/*
+ * Largest n_pix accepted by wst_dft_noalloc (size of its built-in scratch).
+ */
+#define WST_DFT_NOALLOC_MAX_PIX 4096
+
+/*
+ * wst_dft without any device allocation.  (The paper has no counterpart: this is
+ * an interface for a class of callers, not part of the method.)
+ *
+ * Who needs it: code that must not call cudaMalloc, cudaFree or an allocating
+ * library routine -- a real-time pipeline (e.g. a correlator back end) that
+ * forbids allocation after start-up because cudaMalloc/cudaFree can block and
+ * synchronise the device; a component inside an application whose memory pool has
+ * reserved the whole device, so a fresh allocation would fail or fragment it; or a
+ * plug-in that must keep the host application's device footprint fixed.  Such a
+ * caller passes inputs and outputs it already owns; this call brings its own
+ * scratch.
+ *
+ * Same arguments and result as wst_dft (out_i = sum_j w_j V_j exp(2 pi i (u_j l +
+ * v_j m + w_j (n-1))), float-float phases), but the partial sums live in a fixed
+ * 2 MiB array compiled into the library (one per GPU that loads it, kept until the
+ * process exits), reduced by a second pass in a fixed order, so repeated calls give
+ * identical bits and `out` needs no clearing.
+ *
+ * Limits and rules:
+ *   - n_pix <= WST_DFT_NOALLOC_MAX_PIX, else WST_ERR_UNSUPPORTED and nothing runs.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose GPU work overlaps
+ *     (other streams, other host threads) race and corrupt each other's sums.
+ *     Serialise them, e.g. on one stream.
+ *   - Each call writes every scratch slot it later reads; nothing carries over.
+ */
+wst_status wst_dft_noalloc(int64_t n_vis, const float *u, const float *v, const float *w,
+                           const void *vis, const float *weight, int32_t n, double fov,
+                           int64_t n_pix, const int32_t *pa, const int32_t *pb, void *out,
+                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

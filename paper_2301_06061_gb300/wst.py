@@ -31,7 +31,7 @@ EXPORTED = [
     "wst_plan_workspace_bytes", "wst_plan_set_workspace", "wst_plan_set_kernel_table",
     "wst_plan_set_vis", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_degrid",
     "wst_kernel_grad", "wst_vis_cells", "wst_get_stats", "wst_last_error", "wst_dft",
-    "wst_predict_points",
+    "wst_predict_points", "wst_dft_noalloc",
 ]
 
 
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "wst_last_error": ([P], ctypes.c_char_p),
             "wst_dft": ([I64, P, P, P, P, P, I32, D, I64, P, P, P, P], ctypes.c_int),
             "wst_predict_points": ([I64, P, P, P, I64, P, P, P, P, P], ctypes.c_int),
+            "wst_dft_noalloc": ([I64, P, P, P, P, P, I32, D, I64, P, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -253,6 +254,18 @@ def wst_dft(u, v, w, vis, n: int, fov: float, pa, pb, out, weight=None, stream=N
     _check(load_library().wst_dft(u.numel(), _ptr(u), _ptr(v), _ptr(w), _ptr(vis), _ptr(weight), int(n),
                                   float(fov), pa.numel(), _ptr(pa), _ptr(pb), _ptr(out), _stream(stream)),
            "wst_dft")
+
+
+WST_DFT_NOALLOC_MAX_PIX = 4096
+
+
+def wst_dft_noalloc(u, v, w, vis, n: int, fov: float, pa, pb, out, weight=None, stream=None) -> int:
+    """Allocation-free direct transform; returns the status (raises on CUDA errors only)."""
+    rc = load_library().wst_dft_noalloc(u.numel(), _ptr(u), _ptr(v), _ptr(w), _ptr(vis), _ptr(weight), int(n),
+                                        float(fov), pa.numel(), _ptr(pa), _ptr(pb), _ptr(out), _stream(stream))
+    if rc == 3:
+        _check(rc, "wst_dft_noalloc")
+    return rc
 
 
 def wst_predict_points(u, v, w, l, m, flux, out, stream=None) -> None:
