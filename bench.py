@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dft-pixels", type=int, default=64)
+    ap.add_argument("--n-w", type=int, default=0, help="override the number of w-planes (profiling cases)")
+    ap.add_argument("--vis-frac", type=float, default=1.0, help="keep this fraction of the visibilities")
     return ap.parse_args()
 
 
@@ -72,15 +74,17 @@ def load_peaks():
 # workloads (seeded, synthetic; see paper_2301_06061_gb300/synth.py)
 # ------------------------------------------------------------------------------------------
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, n_w: int = 0, vis_frac: float = 1.0):
     from paper_2301_06061_gb300 import synth
 
     if name == "large":
-        work = synth.large(seed_extra=rank)
+        work = synth.large(n_vis=int(100_000_000 * vis_frac), seed_extra=rank)
     elif name == "array":
         work = synth.array(seed_extra=rank)
     else:
         work = synth.batched(seed_extra=rank)
+    if n_w > 0:
+        work.n_w = n_w
     # visibility values do not change any kernel's work: seeded complex Gaussian values
     vis = synth.random_visibilities(work.n_vis, synth.rng_for(3, 7 + rank))
     return work, vis
@@ -233,7 +237,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     build.build()
-    work, vis_np = make_workload(args.workload, rank)
+    work, vis_np = make_workload(args.workload, rank, args.n_w, args.vis_frac)
     n_vis = work.n_vis
     batch = 1 if work.batch_offsets is None else len(work.batch_offsets) - 1
     cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,

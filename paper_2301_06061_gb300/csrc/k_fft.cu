@@ -145,17 +145,32 @@ constexpr int num_stages(int L, int ept) {
   return n;
 }
 
-__device__ __forceinline__ float2 twiddle(const float2 *tw, int idx, int dir) {
-  float2 w = __ldg(tw + idx);
-  if (dir < 0) w.y = -w.y;
-  return w;
+// exp(dir 2 pi i idx / N) from a quarter-wave table T[m] = exp(2 pi i m / N), m < N/4
+// (32 KB at N = 16384, so it stays in L1 next to a whole row in shared memory); the
+// quadrant q = idx div (N/4) is applied as q quarter turns.
+struct Tw {
+  const float2 *t;
+  int qshift;  // log2(N/4)
+  int qmask;   // N/4 - 1
+};
+
+__device__ __forceinline__ float2 twiddle(const Tw &tw, int idx, int dir) {
+  const float2 b = __ldg(tw.t + (idx & tw.qmask));
+  const int q = (idx >> tw.qshift) & 3;
+  float x = (q & 1) ? -b.y : b.x;
+  float y = (q & 1) ? b.x : b.y;
+  if (q & 2) {
+    x = -x;
+    y = -y;
+  }
+  return make_float2(x, dir < 0 ? -y : y);
 }
 
 // Butterfly b of this thread has index j = jt + b * TPL (< L/R); its inputs sit at
 // j + r L/R and, after the twiddles w_{NS R}^{(j mod NS) r} and the radix-R DFT, its
 // outputs belong at (j / NS) NS R + (j mod NS) + r NS.
 template <int L, int EPT, int TPL, int S, int DIR>
-__device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const float2 *tw, int twscale) {
+__device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const Tw &tw, int twscale) {
   constexpr int R = stage_radix(L, EPT, S);
   constexpr int NS = stage_ns(L, EPT, S);
 #pragma unroll
@@ -191,7 +206,7 @@ __device__ __forceinline__ int out_index(int jt, int b, int r) {
 // holds the inputs of the last stage, already loaded.
 template <int L, int EPT, int TPL, int S, int DIR, class SMI>
 __device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *sm, SMI smi,
-                                              const float2 *tw, int twscale) {
+                                              const Tw &tw, int twscale) {
   constexpr int NST = num_stages(L, EPT);
   if constexpr (S < NST) {
     // store outputs of stage S-1
@@ -228,7 +243,7 @@ struct RowCfg {
 
 template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
-k_rows(float2 *__restrict__ planes, const float2 *__restrict__ tw) {
+k_rows(float2 *__restrict__ planes, Tw tw) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -267,6 +282,124 @@ k_rows(float2 *__restrict__ planes, const float2 *__restrict__ tw) {
 }
 
 // ---------------------------------------------------------------------------------
+// pass R for long rows (N >= kRowsTmaMin): a whole padded row fills most of an SM's
+// shared memory, so one CTA per SM loops over rows.  As soon as the last stage has read
+// its inputs out of shared memory, one thread starts TMA bulk copies of the CTA's next
+// row into the freed buffer (mbarrier with transaction count), so the load of row r+1
+// overlaps the last stage and the stores of row r.  Stage 0 reads the row in natural
+// (unpadded) order; later stages use the padded layout.  Every wait is bounded: on
+// timeout the CTA records WST_ERR_TIMEOUT in the device error word and returns.
+// ---------------------------------------------------------------------------------
+constexpr int kRowsTmaMin = 16384;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(mbar, phase)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void tma_load_row(uint32_t dst_smem, const float2 *src, uint32_t mbar) {
+  constexpr int kPiece = 32768;
+  constexpr int kPieces = BYTES / kPiece;
+  static_assert(BYTES % kPiece == 0, "row size");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(BYTES) : "memory");
+#pragma unroll
+  for (int i = 0; i < kPieces; ++i) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_smem + i * kPiece),
+        "l"(reinterpret_cast<const char *>(src) + (size_t)i * kPiece), "r"(kPiece), "r"(mbar)
+        : "memory");
+  }
+}
+
+template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS, 1)
+k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long long *err) {
+  using C = RowCfg<N>;
+  static_assert(C::RPC == 1, "one row per CTA");
+  constexpr int EPT = C::EPT, TPR = C::TPR;
+  constexpr int NST = num_stages(N, EPT);
+  constexpr int R0 = stage_radix(N, EPT, 0);
+  constexpr int RL = stage_radix(N, EPT, NST - 1);
+  extern __shared__ __align__(128) float2 sm_rows[];
+  __shared__ __align__(8) unsigned long long mbar_storage;
+  const int jt = threadIdx.x;
+  auto smi = [](int i) { return i + (i >> 4); };
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm_rows);
+  const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&mbar_storage);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  int64_t row = blockIdx.x;
+  uint32_t phase = 0;
+  if (threadIdx.x == 0 && row < total_rows) tma_load_row<N * 8>(sbase, planes + row * N, mbar);
+  for (; row < total_rows; row += gridDim.x) {
+    const bool ok = mbar_wait_bounded(mbar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, (unsigned long long)WST_ERR_TIMEOUT);
+        mbar_wait_bounded(mbar, phase);  // let a late copy into our buffer land, also bounded
+      }
+      return;
+    }
+    phase ^= 1u;
+    const int q = (int)(row % N);
+    float2 *grow = planes + row * N;
+    float2 v[EPT];
+#pragma unroll
+    for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+        float2 x = sm_rows[idx];  // natural order, as copied
+        if (PRESIGN && ((idx + q) & 1)) x = make_float2(-x.x, -x.y);
+        v[b * R0 + r] = x;
+      }
+    __syncthreads();  // natural-order reads done before the padded writes
+    stage_compute<N, EPT, TPR, 0, DIR>(v, jt, tw, 1);
+    middle_stages<N, EPT, TPR, 1, DIR>(v, jt, sm_rows, smi, tw, 1);
+    __syncthreads();  // every read of this row is done: the buffer is free
+    if (threadIdx.x == 0 && row + gridDim.x < total_rows) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tma_load_row<N * 8>(sbase, planes + (row + gridDim.x) * N, mbar);
+    }
+    stage_compute<N, EPT, TPR, NST - 1, DIR>(v, jt, tw, 1);
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int idx = out_index<N, EPT, TPR, NST - 1>(jt, b, r);
+        float2 x = v[b * RL + r];
+        if (POSTSIGN && ((idx + q) & 1)) x = make_float2(-x.x, -x.y);
+        grow[idx] = x;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // pass CA: four-step column stage A, length-LB lines over rows a + A*i, 16-col bands
 // ---------------------------------------------------------------------------------
 constexpr int kCB = 16;  // columns per band (128 bytes per row segment)
@@ -281,7 +414,7 @@ struct ColCfg {
 
 template <int LB, int DIR, bool TW_FIRST>
 __global__ void __launch_bounds__(ColCfg<LB>::THREADS)
-k_cols_a(float2 *__restrict__ planes, const float2 *__restrict__ tw, int n) {
+k_cols_a(float2 *__restrict__ planes, Tw tw, int n) {
   using C = ColCfg<LB>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LB, EPT);
@@ -324,39 +457,47 @@ k_cols_a(float2 *__restrict__ planes, const float2 *__restrict__ tw, int n) {
 
 // ---------------------------------------------------------------------------------
 // phase screen helpers (K-P)
+//
+// The screen of plane k at pixel (a, b) is e^{2 pi i w_k t}, t = n - 1, with w_k = w_0 +
+// k dw inside an image.  It is evaluated exactly (float-float argument, reduced modulo
+// one cycle) at an anchor plane, and advanced to the next plane by one complex multiply
+// with the pixel's step e^{2 pi i dw t}, itself evaluated exactly at the anchor.  Anchors
+// are the first plane of an image in a chunk and every kAnchor-th plane after it, so
+// the rounding of the recurrence never compounds over more than kAnchor - 1 products.
 // ---------------------------------------------------------------------------------
+constexpr int kAnchor = 8;
+
 struct ScreenCtx {
   const float2 *l2ff;      // l_a^2 float-float
   const double *l2d;       // l_a^2 FP64
   const float2 *wc;        // plane centres float-float (global plane index)
   const double *wcd;       // plane centres FP64
+  const float2 *dwff;      // plane spacing per image, float-float
+  const double *wrange;    // per image: w_lo, scale, dw, w_hi
   const float *corr;       // 1/Ghat
-  int fp64;                // WST_FLAG_FP64_SCREEN
 };
 
-struct PixelScreen {
-  ff t;      // n - 1
-  double td; // n - 1 in FP64 (fp64 mode)
-  bool valid;
-};
-
-__device__ __forceinline__ PixelScreen pixel_screen(const ScreenCtx &sc, int kp, int kq) {
-  PixelScreen ps;
-  const float2 la = sc.l2ff[kp], mb = sc.l2ff[kq];
-  ps.t = n_minus_one_ff(la, mb, ps.valid);
-  ps.td = 0.0;
-  if (sc.fp64 && ps.valid) {
+// exact screen of plane P and per-plane step at pixel (kp, kq), both times `scale`
+template <bool FP64S>
+__device__ __forceinline__ void screen_anchor(const ScreenCtx &sc, int kp, int kq, int P, int img, float scale,
+                                              float2 &scr, float2 &stp) {
+  scr = stp = make_float2(0.0f, 0.0f);
+  if constexpr (FP64S) {
     const double r2 = sc.l2d[kp] + sc.l2d[kq];
-    ps.td = -r2 / (1.0 + sqrt(1.0 - r2));
+    if (!(r2 < 1.0)) return;
+    const double t = -r2 / (1.0 + sqrt(1.0 - r2));
+    scr = cis_cycles_d(sc.wcd[P] * t);
+    stp = cis_cycles_d(sc.wrange[4 * img + 2] * t);
+  } else {
+    bool valid;
+    const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+    if (!valid) return;
+    const float2 w = sc.wc[P], dw = sc.dwff[img];
+    scr = cis_cycles_ff(ff_mul({w.x, w.y}, t));
+    stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
   }
-  return ps;
-}
-
-__device__ __forceinline__ float2 screen_value(const ScreenCtx &sc, const PixelScreen &ps, int P) {
-  if (!ps.valid) return make_float2(0.0f, 0.0f);
-  if (sc.fp64) return cis_cycles_d(sc.wcd[P] * ps.td);
-  const float2 w = sc.wc[P];
-  return cis_cycles_ff(ff_mul({w.x, w.y}, ps.t));
+  scr.x *= scale;
+  scr.y *= scale;
 }
 
 __device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 y) {
@@ -372,12 +513,12 @@ __device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 y) {
 enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
 
 // ---------------------------------------------------------------------------------
-// pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then sign, screen and the
-// compensated sum over the chunk's planes into the image.
+// pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then the centring sign and
+// the screen, and the (Kahan-compensated) sum over the chunk's planes of each image.
 // ---------------------------------------------------------------------------------
-template <int LA>
+template <int LA, bool FP64S>
 __global__ void __launch_bounds__(ColCfg<LA>::THREADS)
-k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const float2 *__restrict__ tw,
+k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
              int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
   using C = ColCfg<LA>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
@@ -390,27 +531,26 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const f
   const int c = blockIdx.y;
   const int kp = blockIdx.x * kCB + col;
   auto smi = [col](int i) { return i * C::PADW + col; };
-  // this thread's output pixels: d = out_index(...), kq = c + B d
-  PixelScreen px[EPT];
-  float sgn[EPT];
-#pragma unroll
-  for (int b = 0; b < EPT / RL; ++b)
-#pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const int d = out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-      const int kq = c + B * d;
-      px[b * RL + r] = pixel_screen(sc, kp, kq);
-      sgn[b * RL + r] = ((kq + kp) & 1) ? -1.0f : 1.0f;
-    }
   const bool kahan = flags & ACC_KAHAN;
   int P = p0;
   while (P < p1) {
     const int img = P / n_w;
+    const int pstart = P;
     const int pend = min(p1, (img + 1) * n_w);
-    float2 s[EPT], cc[EPT];
+    float2 s[EPT], cc[EPT], scr[EPT], stp[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) s[e] = cc[e] = make_float2(0.0f, 0.0f);
     for (; P < pend; ++P) {
+      if ((P - pstart) % kAnchor == 0) {
+#pragma unroll
+        for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) {
+            const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
+            screen_anchor<FP64S>(sc, kp, kq, P, img, ((kq + kp) & 1) ? -1.0f : 1.0f, scr[b * RL + r],
+                                 stp[b * RL + r]);
+          }
+      }
       const float2 *base = planes + (size_t)(P - p0) * n * n + (size_t)(LA * c) * n + kp;
       float2 v[EPT];
 #pragma unroll
@@ -424,10 +564,10 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const f
       }
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
-        const float2 y = cmul(v[e], screen_value(sc, px[e], P));
-        const float2 ys = make_float2(sgn[e] * y.x, sgn[e] * y.y);
-        if (kahan) kahan_add(s[e], cc[e], ys);
-        else s[e] = cadd(s[e], ys);
+        const float2 y = cmul(v[e], scr[e]);
+        if (kahan) kahan_add(s[e], cc[e], y);
+        else s[e] = cadd(s[e], y);
+        scr[e] = cmul(scr[e], stp[e]);
       }
       if constexpr (NST > 1) __syncthreads();  // shared memory reused by the next plane
     }
@@ -442,28 +582,25 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const f
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         const int e = b * RL + r;
-        const int d = out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-        const size_t o = (size_t)(c + B * d) * n + kp;
+        const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
+        const size_t o = (size_t)kq * n + kp;
         float2 sum = s[e], cmp = cc[e];
         if (flags & ACC_STAGED) {
-          float2 old = im[o];
-          im[o] = cadd(old, csub(sum, cmp));
+          im[o] = cadd(im[o], csub(sum, cmp));
           continue;
         }
         if (!first_any) {  // merge with the running (sum, compensation) of earlier chunks
-          const float2 s0 = im[o];
-          const float2 c0 = cp ? cp[o] : make_float2(0.0f, 0.0f);
-          float2 acc_s = s0, acc_c = c0;
+          float2 acc_s = im[o];
+          float2 acc_c = cp ? cp[o] : make_float2(0.0f, 0.0f);
           kahan_add(acc_s, acc_c, sum);
-          float2 negc = make_float2(-cmp.x, -cmp.y);
-          kahan_add(acc_s, acc_c, negc);
+          kahan_add(acc_s, acc_c, make_float2(-cmp.x, -cmp.y));
           sum = acc_s;
           cmp = acc_c;
         }
         if (last_any) {
           float2 out = csub(sum, cmp);
           if (flags & ACC_CORRECT) {
-            const float f = sc.corr[kp] * sc.corr[c + B * d];
+            const float f = sc.corr[kp] * sc.corr[kq];
             out = make_float2(out.x * f, out.y * f);
           }
           im[o] = out;
@@ -478,9 +615,9 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, const f
 // ---------------------------------------------------------------------------------
 // pass CB^H (adjoint): image tile -> planes; sign, correction and conjugate screen fused
 // ---------------------------------------------------------------------------------
-template <int LA>
+template <int LA, bool FP64S>
 __global__ void __launch_bounds__(ColCfg<LA>::THREADS)
-k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, const float2 *__restrict__ tw,
+k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, Tw tw,
           int n, ScreenCtx sc, int correct, float2 *__restrict__ planes) {
   using C = ColCfg<LA>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
@@ -494,21 +631,8 @@ k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, const floa
   const int kp = blockIdx.x * kCB + col;
   auto smi = [col](int i) { return i * C::PADW + col; };
   // inputs of the first stage: element d <-> image row kq = c + B d
-  PixelScreen px[EPT];
-  float scale[EPT];
-  float2 dv[EPT];
-  int img_loaded = -1;
-#pragma unroll
-  for (int b = 0; b < EPT / R0; ++b)
-#pragma unroll
-    for (int r = 0; r < R0; ++r) {
-      const int d = in_index<LA, EPT, TPL, 0>(jt, b, r);
-      const int kq = c + B * d;
-      px[b * R0 + r] = pixel_screen(sc, kp, kq);
-      float f = ((kq + kp) & 1) ? -1.0f : 1.0f;
-      if (correct) f *= sc.corr[kp] * sc.corr[kq];
-      scale[b * R0 + r] = f;
-    }
+  float2 dv[EPT], scr[EPT], stp[EPT];
+  int img_loaded = -1, pstart = p0;
   for (int P = p0; P < p1; ++P) {
     const int img = P / n_w;
     if (img != img_loaded) {
@@ -521,12 +645,27 @@ k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, const floa
           dv[b * R0 + r] = im[(size_t)(c + B * d) * n + kp];
         }
       img_loaded = img;
+      pstart = P;
+    }
+    if ((P - pstart) % kAnchor == 0) {
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int kq = c + B * in_index<LA, EPT, TPL, 0>(jt, b, r);
+          float f = ((kq + kp) & 1) ? -1.0f : 1.0f;
+          if (correct) f *= sc.corr[kp] * sc.corr[kq];
+          float2 a, st;
+          screen_anchor<FP64S>(sc, kp, kq, P, img, f, a, st);
+          scr[b * R0 + r] = make_float2(a.x, -a.y);  // conjugate screen
+          stp[b * R0 + r] = make_float2(st.x, -st.y);
+        }
     }
     float2 v[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const float2 y = cmulc(dv[e], screen_value(sc, px[e], P));  // conj(screen) * D
-      v[e] = make_float2(scale[e] * y.x, scale[e] * y.y);
+      v[e] = cmul(dv[e], scr[e]);
+      scr[e] = cmul(scr[e], stp[e]);
     }
     stage_compute<LA, EPT, TPL, 0, -1>(v, jt, tw, B);
     if constexpr (NST > 1) {
@@ -557,32 +696,52 @@ __global__ void k_correct(float2 *image, const float *corr, int n, int64_t total
 // ---------------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------------
+static Tw tw_of(const wst_plan_s *p) {
+  Tw t;
+  t.t = p->tw;
+  t.qshift = p->log2n - 2;
+  t.qmask = (p->n >> 2) - 1;
+  return t;
+}
+
 template <int N, int DIR, bool PRE, bool POST>
-static cudaError_t launch_rows(float2 *planes, int nplanes, const float2 *tw, cudaStream_t s) {
+static cudaError_t launch_rows(wst_plan_s *p, float2 *planes, int nplanes) {
   using C = RowCfg<N>;
   const size_t smem = sizeof(float2) * C::RPC * C::PADL;
-  auto kern = k_rows<N, DIR, PRE, POST>;
-  if (smem > 48 * 1024) {
+  if constexpr (N >= kRowsTmaMin) {
+    auto kern = k_rows_tma<N, DIR, PRE, POST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = (int64_t)nplanes * N;
+    const int grid = (int)(rows < sms ? rows : sms);
+    kern<<<grid, C::THREADS, smem, p->stream>>>(planes, rows, tw_of(p), p->W_.counters + CNT_ERROR);
+  } else {
+    auto kern = k_rows<N, DIR, PRE, POST>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grd(N / C::RPC, nplanes);
+    kern<<<grd, C::THREADS, smem, p->stream>>>(planes, tw_of(p));
   }
-  dim3 grd(N / C::RPC, nplanes);
-  kern<<<grd, C::THREADS, smem, s>>>(planes, tw);
   return cudaGetLastError();
 }
 
 template <int DIR, bool PRE, bool POST>
-static cudaError_t rows_dispatch(int n, float2 *planes, int nplanes, const float2 *tw, cudaStream_t s) {
-  switch (n) {
-    case 64: return launch_rows<64, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 128: return launch_rows<128, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 256: return launch_rows<256, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 512: return launch_rows<512, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 1024: return launch_rows<1024, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 2048: return launch_rows<2048, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 4096: return launch_rows<4096, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 8192: return launch_rows<8192, DIR, PRE, POST>(planes, nplanes, tw, s);
-    case 16384: return launch_rows<16384, DIR, PRE, POST>(planes, nplanes, tw, s);
+static cudaError_t rows_dispatch(wst_plan_s *p, float2 *planes, int nplanes) {
+  switch (p->n) {
+    case 64: return launch_rows<64, DIR, PRE, POST>(p, planes, nplanes);
+    case 128: return launch_rows<128, DIR, PRE, POST>(p, planes, nplanes);
+    case 256: return launch_rows<256, DIR, PRE, POST>(p, planes, nplanes);
+    case 512: return launch_rows<512, DIR, PRE, POST>(p, planes, nplanes);
+    case 1024: return launch_rows<1024, DIR, PRE, POST>(p, planes, nplanes);
+    case 2048: return launch_rows<2048, DIR, PRE, POST>(p, planes, nplanes);
+    case 4096: return launch_rows<4096, DIR, PRE, POST>(p, planes, nplanes);
+    case 8192: return launch_rows<8192, DIR, PRE, POST>(p, planes, nplanes);
+    case 16384: return launch_rows<16384, DIR, PRE, POST>(p, planes, nplanes);
   }
   return cudaErrorInvalidValue;
 }
@@ -590,16 +749,16 @@ static cudaError_t rows_dispatch(int n, float2 *planes, int nplanes, const float
 cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool presign, bool postsign) {
   if (nplanes <= 0) return cudaSuccess;
   p->launches += 1;
-  if (dir > 0 && !presign && !postsign) return rows_dispatch<1, false, false>(p->n, planes, nplanes, p->tw, p->stream);
-  if (dir > 0 && presign && !postsign) return rows_dispatch<1, true, false>(p->n, planes, nplanes, p->tw, p->stream);
-  if (dir < 0 && !presign && postsign) return rows_dispatch<-1, false, true>(p->n, planes, nplanes, p->tw, p->stream);
+  if (dir > 0 && !presign && !postsign) return rows_dispatch<1, false, false>(p, planes, nplanes);
+  if (dir > 0 && presign && !postsign) return rows_dispatch<1, true, false>(p, planes, nplanes);
+  if (dir < 0 && !presign && postsign) return rows_dispatch<-1, false, true>(p, planes, nplanes);
   return cudaErrorInvalidValue;
 }
 
 template <int LB, int DIR, bool TWF>
 static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes) {
   dim3 grd(p->n / kCB, p->n / LB, nplanes);
-  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, p->tw, p->n);
+  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n);
   return cudaGetLastError();
 }
 
@@ -629,17 +788,24 @@ static ScreenCtx screen_ctx(wst_plan_s *p) {
   sc.l2d = p->l2d;
   sc.wc = p->wcentre;
   sc.wcd = p->wcentre_d;
+  sc.dwff = p->dwff;
+  sc.wrange = p->wrange;
   sc.corr = p->corr;
-  sc.fp64 = (p->cfg.flags & WST_FLAG_FP64_SCREEN) ? 1 : 0;
   return sc;
 }
+
+static bool fp64_screen(const wst_plan_s *p) { return (p->cfg.flags & WST_FLAG_FP64_SCREEN) != 0; }
 
 template <int LA>
 static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                  float2 *comp, int flags) {
   dim3 grd(p->n / kCB, p->n / LA);
-  k_cols_b_acc<LA><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, p->tw, p->n,
-                                                                screen_ctx(p), image, comp, flags);
+  if (fp64_screen(p))
+    k_cols_b_acc<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
+                                                                        screen_ctx(p), image, comp, flags);
+  else
+    k_cols_b_acc<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
+                                                                         screen_ctx(p), image, comp, flags);
   return cudaGetLastError();
 }
 
@@ -665,8 +831,12 @@ template <int LA>
 static cudaError_t launch_cols_bh(wst_plan_s *p, const float2 *dimage, int p0, int p1, float2 *planes,
                                   bool correct) {
   dim3 grd(p->n / kCB, p->n / LA);
-  k_cols_bh<LA><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, p->tw, p->n,
-                                                             screen_ctx(p), correct ? 1 : 0, planes);
+  if (fp64_screen(p))
+    k_cols_bh<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, tw_of(p), p->n,
+                                                                     screen_ctx(p), correct ? 1 : 0, planes);
+  else
+    k_cols_bh<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, tw_of(p), p->n,
+                                                                      screen_ctx(p), correct ? 1 : 0, planes);
   return cudaGetLastError();
 }
 

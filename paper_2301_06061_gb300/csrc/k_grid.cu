@@ -53,30 +53,55 @@ __device__ __forceinline__ float frac24(uint32_t pack) {
   return (float)(pack & 0xFFFFFFu) * (1.0f / 16777216.0f);
 }
 
-// grid plane chunk [p0, p0 + gridDim-planes): blockIdx.x = tile, blockIdx.y = plane offset
+// grid plane chunk [p0, p0 + gridDim-planes): blockIdx.x = tile, blockIdx.y = plane offset.
+// W is a template parameter so that the tap map t -> (t mod W, t div W) is hoisted out of
+// the per-visibility loop.
+template <int W>
 __global__ void __launch_bounds__(kGridThreads)
 k_grid_tiles(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int tiles,
              int n, KernelParams kp, float2 *__restrict__ out, int checker) {
   extern __shared__ float smem[];
-  const int W = kp.support;
-  const int S = kTile + W;  // row stride (floats), == W mod 32
+  constexpr int S = kTile + W;  // row stride (floats), == W mod 32
   float *sre = smem;
   float *sim = smem + kTile * S;
   const int tx = blockIdx.x % tiles, ty = blockIdx.x / tiles;
   const int pl = blockIdx.y;
   const int P = p0 + pl;
+  uint32_t beg[4], end[4];
+  int dx[4], dy[4];
+  bucket_ranges(off, (int64_t)P * tiles, tiles, tx, ty, beg, end, dx, dy);
+  float2 *dst_plane = out + (size_t)pl * n * n;
+  if (end[0] == beg[0] && end[1] == beg[1] && end[2] == beg[2] && end[3] == beg[3]) {
+    // no visibility reaches this tile (most of them): write its zeros and leave
+    float4 *dst = reinterpret_cast<float4 *>(dst_plane);
+    const int half_t = kTile / 2;
+    for (int e = threadIdx.x; e < kTile * half_t; e += kGridThreads) {
+      const int row = e / half_t, c2 = (e % half_t) * 2;
+      dst[((size_t)(ty * kTile + row) * n + tx * kTile + c2) >> 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < kTile * S; i += kGridThreads) {
     sre[i] = 0.0f;
     sim[i] = 0.0f;
   }
-  uint32_t beg[4], end[4];
-  int dx[4], dy[4];
-  bucket_ranges(off, (int64_t)P * tiles, tiles, tx, ty, beg, end, dx, dy);
   __syncthreads();
 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int WW = W * W;
-  const int rounds = (WW + 31) >> 5;
+  constexpr int WW = W * W;
+  constexpr int ROUNDS = (WW + 31) / 32;
+  // this lane's taps: t = lane + 32 it -> column a, row b of the footprint
+  int ta[ROUNDS], tb[ROUNDS];
+  bool tv[ROUNDS];
+#pragma unroll
+  for (int it = 0; it < ROUNDS; ++it) {
+    const int t = lane + 32 * it;
+    tv[it] = t < WW;
+    ta[it] = tv[it] ? t % W : 0;
+    tb[it] = tv[it] ? t / W : 0;
+  }
+  const int tap = lane & 15;
+  const float targ0 = (float)tap - 0.5f * (float)W;
 #pragma unroll 1
   for (int rg = 0; rg < 4; ++rg) {
     const uint32_t b0 = beg[rg], cnt = end[rg] - beg[rg];
@@ -95,19 +120,14 @@ k_grid_tiles(const Record *__restrict__ rec, const uint32_t *__restrict__ off, i
         const int cx = (int)(xp >> kFracBits) + dx[rg];
         const int cy = (int)(yp >> kFracBits) + dy[rg];
         // lanes 0..15 -> u-profile tap `lane`, lanes 16..31 -> v-profile tap `lane - 16`
-        const int tap = lane & 15;
         const float g = (lane < 16) ? frac24(xp) : frac24(yp);
-        const float prof = (tap < W) ? kernel_eval(kp, (float)tap - kp.half + g) : 0.0f;
-#pragma unroll 1
-        for (int it = 0; it < rounds; ++it) {
-          const int t = lane + 32 * it;
-          const bool valid = t < WW;
-          const int a = valid ? t % W : 0;
-          const int bb = valid ? t / W : 0;
-          const float ga = __shfl_sync(0xFFFFFFFFu, prof, a);
-          const float gb = __shfl_sync(0xFFFFFFFFu, prof, 16 + bb);
-          const int px = cx + a, py = cy + bb;
-          if (valid && px >= 0 && px < kTile && py >= 0 && py < kTile) {
+        const float prof = (tap < W) ? kernel_eval(kp, targ0 + g) : 0.0f;
+#pragma unroll
+        for (int it = 0; it < ROUNDS; ++it) {
+          const float ga = __shfl_sync(0xFFFFFFFFu, prof, ta[it]);
+          const float gb = __shfl_sync(0xFFFFFFFFu, prof, 16 + tb[it]);
+          const int px = cx + ta[it], py = cy + tb[it];
+          if (tv[it] && (unsigned)px < (unsigned)kTile && (unsigned)py < (unsigned)kTile) {
             const float wgt = ga * gb;
             atomicAdd(&sre[py * S + px], vre * wgt);
             atomicAdd(&sim[py * S + px], vim * wgt);
@@ -117,33 +137,36 @@ k_grid_tiles(const Record *__restrict__ rec, const uint32_t *__restrict__ off, i
     }
   }
   __syncthreads();
-  // flush: two cells per 16-byte store; optional (-1)^(p+q) centring sign
-  float4 *dst = reinterpret_cast<float4 *>(out + (size_t)pl * n * n);
-  const int half_t = kTile / 2;
-  for (int e = threadIdx.x; e < kTile * half_t; e += kGridThreads) {
-    const int row = e / half_t, c2 = (e % half_t) * 2;
-    const int q = ty * kTile + row, p = tx * kTile + c2;
-    float s = 1.0f;
-    if (checker && ((p + q) & 1)) s = -1.0f;
-    const float s2 = checker ? -s : s;
-    float4 val = make_float4(s * sre[row * S + c2], s * sim[row * S + c2], s2 * sre[row * S + c2 + 1],
-                             s2 * sim[row * S + c2 + 1]);
-    dst[((size_t)q * n + p) >> 1] = val;
+  // flush: one cell per thread and step (consecutive columns: conflict-free shared reads,
+  // coalesced 8-byte stores); optional (-1)^(p+q) centring sign
+  for (int e = threadIdx.x; e < kTile * kTile; e += kGridThreads) {
+    const int row = e / kTile, col = e % kTile;
+    const int q = ty * kTile + row, p = tx * kTile + col;
+    const float sg = (checker && ((p + q) & 1)) ? -1.0f : 1.0f;
+    dst_plane[(size_t)q * n + p] = make_float2(sg * sre[row * S + col], sg * sim[row * S + col]);
   }
+}
+
+template <int W>
+static void launch_grid(wst_plan_s *p, int p0, int np, float2 *out, bool checker) {
+  const size_t smem = sizeof(float) * 2 * kTile * (kTile + W);
+  dim3 grd(p->tiles * p->tiles, np);
+  k_grid_tiles<W><<<grd, kGridThreads, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, p->tiles, p->n,
+                                                          kernel_params(p), out, checker ? 1 : 0);
 }
 
 cudaError_t grid_planes(wst_plan_s *p, int p0, int p1, float2 *out, bool checker) {
   const int np = p1 - p0;
   if (np <= 0) return cudaSuccess;
-  const size_t smem = sizeof(float) * 2 * kTile * (kTile + p->W);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_grid_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
+  switch (p->W) {
+#define WST_GRID_CASE(w) \
+  case w: launch_grid<w>(p, p0, np, out, checker); break;
+    WST_GRID_CASE(2) WST_GRID_CASE(3) WST_GRID_CASE(4) WST_GRID_CASE(5) WST_GRID_CASE(6) WST_GRID_CASE(7)
+    WST_GRID_CASE(8) WST_GRID_CASE(9) WST_GRID_CASE(10) WST_GRID_CASE(11) WST_GRID_CASE(12)
+    WST_GRID_CASE(13) WST_GRID_CASE(14) WST_GRID_CASE(15) WST_GRID_CASE(16)
+#undef WST_GRID_CASE
+    default: return cudaErrorInvalidValue;
   }
-  dim3 grd(p->tiles * p->tiles, np);
-  k_grid_tiles<<<grd, kGridThreads, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, p->tiles,
-                                                       p->n, kernel_params(p), out, checker ? 1 : 0);
   p->launches += 1;
   return cudaGetLastError();
 }

@@ -21,10 +21,10 @@ KernelParams kernel_params(const wst_plan_s *p) {
   return k;
 }
 
-// exp(+2 pi i m / N), rounded once from FP64
+// quarter-wave table exp(+2 pi i m / N), m < N/4, rounded once from FP64
 __global__ void k_twiddles(float2 *tw, int n) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= n) return;
+  if (m >= n / 4) return;
   double s, c;
   sincospi(2.0 * (double)m / (double)n, &s, &c);
   tw[m] = make_float2((float)c, (float)s);
@@ -108,7 +108,7 @@ __device__ __forceinline__ float ordered_to_float(uint32_t o) {
   return __uint_as_float(b);
 }
 
-__global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre_d,
+__global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre_d, float2 *dwff,
                                 const uint32_t *wminmax, int batch, int n_w, double cfg_lo,
                                 double cfg_hi, int from_data) {
   int img = blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,6 +129,7 @@ __global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre
   wrange[4 * img + 1] = scale;
   wrange[4 * img + 2] = dw;
   wrange[4 * img + 3] = hi;
+  dwff[img] = ff_split(dw);
   for (int k = 0; k < n_w; ++k) {
     double wk = lo + ((double)k + 0.5) * dw;
     wcentre[img * n_w + k] = ff_split(wk);
@@ -139,7 +140,7 @@ __global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre
 cudaError_t build_plane_centres(wst_plan_s *p) {
   const bool from_data = p->cfg.w_min == p->cfg.w_max;
   k_plane_centres<<<(p->batch + 63) / 64, 64, 0, p->stream>>>(
-      p->wrange, p->wcentre, p->wcentre_d, p->W_.wminmax, p->batch, p->n_w, p->cfg.w_min,
+      p->wrange, p->wcentre, p->wcentre_d, p->dwff, p->W_.wminmax, p->batch, p->n_w, p->cfg.w_min,
       p->cfg.w_max, from_data ? 1 : 0);
   p->launches += 1;
   return cudaGetLastError();

@@ -91,6 +91,7 @@ void destroy_tables(wst_plan_s *p) {
   cudaFree(p->wrange);
   cudaFree(p->wcentre);
   cudaFree(p->wcentre_d);
+  cudaFree(p->dwff);
   cudaFree(p->batch_off);
   for (auto *l : {&p->ev_sort, &p->ev_img})
     for (auto e : l->ev) cudaEventDestroy(e);
@@ -191,6 +192,7 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   ALLOC(p->wrange, 4 * c.batch);
   ALLOC(p->wcentre, p->n_planes);
   ALLOC(p->wcentre_d, p->n_planes);
+  ALLOC(p->dwff, c.batch);
   ALLOC(p->batch_off, c.batch + 1);
   if (c.kernel == WST_KERNEL_TABLE) ALLOC(p->ktable, c.ktable_len);
 #undef ALLOC

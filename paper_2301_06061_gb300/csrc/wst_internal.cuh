@@ -75,6 +75,7 @@ struct wst_plan_s {
   double *wrange = nullptr;  // per image: w_lo, scale = n_w/(w_hi-w_lo), dw, w_hi
   float2 *wcentre = nullptr; // per global plane: centre w_k as float-float
   double *wcentre_d = nullptr;  // per global plane: centre w_k (FP64)
+  float2 *dwff = nullptr;    // per image: plane spacing dw as float-float
   bool table_set = false;
   // workspace
   char *ws = nullptr;
