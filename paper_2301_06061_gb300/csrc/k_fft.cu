@@ -89,6 +89,29 @@ __device__ __forceinline__ void dft(float2 *v) {
     v[6] = csub(e2, o2);
     v[3] = cadd(e3, o3);
     v[7] = csub(e3, o3);
+  } else if constexpr (R == 32) {
+    // 32 = 2 x 16: X[m] = E[m] + w32^m O[m], X[m + 16] = E[m] - w32^m O[m]
+    constexpr float c32[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                              0.83146961230254523708f, 0.70710678118654752440f, 0.55557023301960222474f,
+                              0.38268343236508977173f, 0.19509032201612826785f, 0.0f};
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<16, DIR>(e);
+    dft<16, DIR>(o);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      // w32^m = cos(pi m/16) + DIR i sin(pi m/16)
+      const float c = m <= 8 ? c32[m] : -c32[16 - m];
+      const float sn = m <= 8 ? c32[8 - m] : c32[m - 8];
+      const float sd = DIR > 0 ? sn : -sn;
+      const float2 t = make_float2(o[m].x * c - o[m].y * sd, o[m].x * sd + o[m].y * c);
+      v[m] = cadd(e[m], t);
+      v[m + 16] = csub(e[m], t);
+    }
   } else {
     static_assert(R == 16, "radix");
     // 16 = 4 x 4: inputs r1 + 4 r2, outputs m2 + 4 m1
@@ -145,25 +168,19 @@ constexpr int num_stages(int L, int ept) {
   return n;
 }
 
-// exp(dir 2 pi i idx / N) from a quarter-wave table T[m] = exp(2 pi i m / N), m < N/4
-// (32 KB at N = 16384, so it stays in L1 next to a whole row in shared memory); the
-// quadrant q = idx div (N/4) is applied as q quarter turns.
+// exp(dir 2 pi i idx / N) from a half-wave table T[m] = exp(2 pi i m / N), m < N/2
+// (64 KB at N = 16384); exp(2 pi i (m + N/2) / N) = -T[m].
 struct Tw {
   const float2 *t;
-  int qshift;  // log2(N/4)
-  int qmask;   // N/4 - 1
+  int hmask;  // N/2 - 1
+  int hbit;   // N/2
 };
 
 __device__ __forceinline__ float2 twiddle(const Tw &tw, int idx, int dir) {
-  const float2 b = __ldg(tw.t + (idx & tw.qmask));
-  const int q = (idx >> tw.qshift) & 3;
-  float x = (q & 1) ? -b.y : b.x;
-  float y = (q & 1) ? b.x : b.y;
-  if (q & 2) {
-    x = -x;
-    y = -y;
-  }
-  return make_float2(x, dir < 0 ? -y : y);
+  float2 w = __ldg(tw.t + (idx & tw.hmask));
+  if (idx & tw.hbit) w = make_float2(-w.x, -w.y);
+  if (dir < 0) w.y = -w.y;
+  return w;
 }
 
 // Butterfly b of this thread has index j = jt + b * TPL (< L/R); its inputs sit at
@@ -234,11 +251,13 @@ __device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *
 // ---------------------------------------------------------------------------------
 template <int N>
 struct RowCfg {
-  static constexpr int EPT = N >= 16 ? 16 : N;
+  // 32 elements per thread for the longest rows: radix 32, 32, 16 (two shared-memory
+  // round trips); 16 otherwise.  Rows are padded by one element every EPT elements.
+  static constexpr int EPT = N >= 16384 ? 32 : (N >= 16 ? 16 : N);
   static constexpr int TPR = N / EPT;
   static constexpr int RPC = TPR >= 256 ? 1 : 256 / TPR;
   static constexpr int THREADS = TPR * RPC;
-  static constexpr int PADL = N + N / 16;
+  static constexpr int PADL = N + N / EPT;
 };
 
 template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
@@ -252,7 +271,7 @@ k_rows(float2 *__restrict__ planes, Tw tw) {
   const int q = blockIdx.x * C::RPC + rl;
   float2 *row = planes + ((size_t)blockIdx.y * N + q) * N;
   float2 *srow = sm_rows + rl * C::PADL;
-  auto smi = [](int i) { return i + (i >> 4); };
+  auto smi = [](int i) { return i + i / EPT; };
   float2 v[EPT];
   constexpr int R0 = stage_radix(N, EPT, 0);
 #pragma unroll
@@ -345,7 +364,7 @@ k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long
   extern __shared__ __align__(128) float2 sm_rows[];
   __shared__ __align__(8) unsigned long long mbar_storage;
   const int jt = threadIdx.x;
-  auto smi = [](int i) { return i + (i >> 4); };
+  auto smi = [](int i) { return i + i / EPT; };
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm_rows);
   const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&mbar_storage);
   if (threadIdx.x == 0) {
@@ -357,12 +376,15 @@ k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long
   uint32_t phase = 0;
   if (threadIdx.x == 0 && row < total_rows) tma_load_row<N * 8>(sbase, planes + row * N, mbar);
   for (; row < total_rows; row += gridDim.x) {
-    const bool ok = mbar_wait_bounded(mbar, phase);
+    // one warp polls the barrier; the others wait at the CTA barrier without issuing
+    bool ok = true;
+    if (threadIdx.x < 32) ok = mbar_wait_bounded(mbar, phase);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, (unsigned long long)WST_ERR_TIMEOUT);
         mbar_wait_bounded(mbar, phase);  // let a late copy into our buffer land, also bounded
       }
+      __syncthreads();
       return;
     }
     phase ^= 1u;
@@ -699,8 +721,8 @@ __global__ void k_correct(float2 *image, const float *corr, int n, int64_t total
 static Tw tw_of(const wst_plan_s *p) {
   Tw t;
   t.t = p->tw;
-  t.qshift = p->log2n - 2;
-  t.qmask = (p->n >> 2) - 1;
+  t.hmask = (p->n >> 1) - 1;
+  t.hbit = p->n >> 1;
   return t;
 }
 

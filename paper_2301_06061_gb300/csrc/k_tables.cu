@@ -21,10 +21,10 @@ KernelParams kernel_params(const wst_plan_s *p) {
   return k;
 }
 
-// quarter-wave table exp(+2 pi i m / N), m < N/4, rounded once from FP64
+// half-wave table exp(+2 pi i m / N), m < N/2, rounded once from FP64
 __global__ void k_twiddles(float2 *tw, int n) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= n / 4) return;
+  if (m >= n / 2) return;
   double s, c;
   sincospi(2.0 * (double)m / (double)n, &s, &c);
   tw[m] = make_float2((float)c, (float)s);
