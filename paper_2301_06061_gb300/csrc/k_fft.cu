@@ -538,8 +538,31 @@ enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
 // pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then the centring sign and
 // the screen, and the (Kahan-compensated) sum over the chunk's planes of each image.
 // ---------------------------------------------------------------------------------
+// 16-byte asynchronous global -> shared copies (sm_80+ LDGSTS), grouped per plane
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The tile of plane P (rows A c .. A c + A - 1, 16 columns) is copied into one of two
+// shared staging buffers while the previous plane is transformed, so the strided loads
+// of the tile never stall the FFT.
+template <int LA>
+__device__ __forceinline__ void stage_tile_async(float2 *buf, const float2 *plane, int n, int row0, int col0) {
+  constexpr int CHUNKS = LA * (kCB * 8 / 16);  // 16-byte pieces per tile
+  const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+  for (int i = threadIdx.x; i < CHUNKS; i += ColCfg<LA>::THREADS) {
+    const int row = i / (kCB / 2), part = i % (kCB / 2);
+    cp_async16(sbuf + (uint32_t)(row * kCB + 2 * part) * 8u, plane + (size_t)(row0 + row) * n + col0 + 2 * part);
+  }
+}
+
 template <int LA, bool FP64S>
-__global__ void __launch_bounds__(ColCfg<LA>::THREADS)
+__global__ void __launch_bounds__(ColCfg<LA>::THREADS, ColCfg<LA>::THREADS >= 32 ? 512 / ColCfg<LA>::THREADS : 1)
 k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
              int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
   using C = ColCfg<LA>;
@@ -548,12 +571,17 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   constexpr int RL = stage_radix(LA, EPT, NST - 1);
   constexpr int R0 = stage_radix(LA, EPT, 0);
   __shared__ float2 sm[LA * C::PADW];
+  __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int kp = blockIdx.x * kCB + col;
+  const int col0 = blockIdx.x * kCB;
+  const int kp = col0 + col;
   auto smi = [col](int i) { return i * C::PADW + col; };
   const bool kahan = flags & ACC_KAHAN;
+  const size_t plane_elems = (size_t)n * n;
+  stage_tile_async<LA>(stage_buf[0], planes, n, LA * c, col0);
+  cp_async_commit();
   int P = p0;
   while (P < p1) {
     const int img = P / n_w;
@@ -563,6 +591,12 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
 #pragma unroll
     for (int e = 0; e < EPT; ++e) s[e] = cc[e] = make_float2(0.0f, 0.0f);
     for (; P < pend; ++P) {
+      // prefetch the next plane's tile, then wait for this plane's
+      if (P + 1 < p1) stage_tile_async<LA>(stage_buf[(P + 1 - p0) & 1], planes + (size_t)(P + 1 - p0) * plane_elems, n,
+                                           LA * c, col0);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
       if ((P - pstart) % kAnchor == 0) {
 #pragma unroll
         for (int b = 0; b < EPT / RL; ++b)
@@ -573,12 +607,12 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
                                  stp[b * RL + r]);
           }
       }
-      const float2 *base = planes + (size_t)(P - p0) * n * n + (size_t)(LA * c) * n + kp;
+      const float2 *tile = stage_buf[(P - p0) & 1];
       float2 v[EPT];
 #pragma unroll
       for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
-        for (int r = 0; r < R0; ++r) v[b * R0 + r] = base[(size_t)in_index<LA, EPT, TPL, 0>(jt, b, r) * n];
+        for (int r = 0; r < R0; ++r) v[b * R0 + r] = tile[in_index<LA, EPT, TPL, 0>(jt, b, r) * kCB + col];
       stage_compute<LA, EPT, TPL, 0, 1>(v, jt, tw, B);
       if constexpr (NST > 1) {
         middle_stages<LA, EPT, TPL, 1, 1>(v, jt, sm, smi, tw, B);
@@ -591,7 +625,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
         else s[e] = cadd(s[e], y);
         scr[e] = cmul(scr[e], stp[e]);
       }
-      if constexpr (NST > 1) __syncthreads();  // shared memory reused by the next plane
+      __syncthreads();  // staging buffer and shared memory reused by the next planes
     }
     // flush this image's tile: its sum starts in this chunk if its first plane is at
     // or after p0, and is complete if its last plane is before p1
