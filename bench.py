@@ -58,6 +58,12 @@ def parse():
     ap.add_argument("--dft-pixels", type=int, default=64)
     ap.add_argument("--n-w", type=int, default=0, help="override the number of w-planes (profiling cases)")
     ap.add_argument("--vis-frac", type=float, default=1.0, help="keep this fraction of the visibilities")
+    ap.add_argument("--snap-w", action="store_true",
+                    help="place every w on its plane centre, so the error against the direct transform is "
+                         "the (u,v) kernel's alone (kernel comparisons)")
+    ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8"], default="gauss",
+                    help="gauss: W=7 Gaussian (the paper's); gauss8 / learned: W=8 Gaussian or the trained "
+                         "table (paper_2301_06061_gb300/data/learned_kernel_w8.npz)")
     return ap.parse_args()
 
 
@@ -238,17 +244,35 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     build.build()
     work, vis_np = make_workload(args.workload, rank, args.n_w, args.vis_frac)
+    if args.snap_w:
+        lo, hi = float(work.w.min()), float(work.w.max())
+        k = np.clip(np.floor((work.w.astype(np.float64) - lo) * (work.n_w / (hi - lo))), 0, work.n_w - 1)
+        work.w = (lo + (k + 0.5) * (hi - lo) / work.n_w).astype(np.float32)
+        work.w_min, work.w_max = lo, hi
     n_vis = work.n_vis
     batch = 1 if work.batch_offsets is None else len(work.batch_offsets) - 1
-    cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
-                     support=work.support, kparam=wst.DEFAULT_SIGMA[work.support],
-                     flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING, planes_per_chunk=args.chunk, batch=batch)
     dev = torch.device("cuda", local_rank)
+    table = None
+    if args.kernel == "gauss":
+        kcfg = dict(support=work.support, kparam=wst.DEFAULT_SIGMA[work.support])
+    elif args.kernel == "gauss8":
+        kcfg = dict(support=8, kparam=wst.DEFAULT_SIGMA[8])
+    else:
+        from paper_2301_06061_gb300 import learned
+
+        tab_np = learned.load_table(os.path.join(ROOT, "paper_2301_06061_gb300", "data", "learned_kernel_w8.npz"))
+        table = torch.from_numpy(tab_np).to(dev)
+        kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
+    cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
+                     flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING, planes_per_chunk=args.chunk, batch=batch,
+                     **kcfg)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_u, h_v, h_w, h_vis = pin(work.u), pin(work.v), pin(work.w), pin(vis_np)
     d_u, d_v, d_w, d_vis = (t.to(dev) for t in (h_u, h_v, h_w, h_vis))
     offsets = None if work.batch_offsets is None else [int(x) for x in work.batch_offsets]
     plan = wst.Plan(cfg, device=dev)
+    if table is not None:
+        plan.set_kernel_table(table)
     img = torch.empty((batch, work.n, work.n), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -368,7 +392,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
-                       "n_vis": n_vis, "batch": batch, "planes_per_chunk": args.chunk or planes,
+                       "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w, "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},
