@@ -19,246 +19,9 @@
 //
 // Twiddles come from one table exp(+2 pi i m/N) rounded once from FP64; every
 // sub-length L divides N, so w_L^m = tw[m N/L].
-#include "wst_internal.cuh"
+#include "fft_core.cuh"
 
 namespace wst {
-
-// ---------------------------------------------------------------------------------
-// register DFTs of radix 2, 4, 8, 16 (natural order in and out), sign DIR
-// ---------------------------------------------------------------------------------
-constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
-constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
-constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
-
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-template <int DIR>
-__device__ __forceinline__ float2 mul_i(float2 a) {  // a * (DIR * i)
-  return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-}
-// a * exp(DIR * 2 pi i k / 16), k a compile-time constant in [0, 16)
-template <int DIR, int K>
-__device__ __forceinline__ float2 mul_w16(float2 a) {
-  constexpr int k = K & 15;
-  if constexpr (k == 0) return a;
-  else if constexpr (k == 4) return mul_i<DIR>(a);
-  else if constexpr (k == 8) return make_float2(-a.x, -a.y);
-  else if constexpr (k == 12) return mul_i<-DIR>(a);
-  else {
-    // cos / sin of 2 pi k / 16 from the three constants
-    constexpr float cs[16] = {1.0f, kC16, kC8, kS16, 0.0f, -kS16, -kC8, -kC16,
-                              -1.0f, -kC16, -kC8, -kS16, 0.0f, kS16, kC8, kC16};
-    constexpr float c = cs[k];
-    constexpr float s = cs[(k + 12) & 15];  // sin(x) = cos(x - pi/2)
-    const float sd = DIR > 0 ? s : -s;
-    return make_float2(a.x * c - a.y * sd, a.x * sd + a.y * c);
-  }
-}
-
-template <int DIR>
-__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
-  const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_i<DIR>(csub(b, d));
-  a = cadd(t0, t2);
-  c = csub(t0, t2);
-  b = cadd(t1, t3);
-  d = csub(t1, t3);
-}
-
-template <int R, int DIR>
-__device__ __forceinline__ void dft(float2 *v) {
-  if constexpr (R == 1) {
-  } else if constexpr (R == 2) {
-    const float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
-  } else if constexpr (R == 4) {
-    dft4<DIR>(v[0], v[1], v[2], v[3]);
-  } else if constexpr (R == 8) {
-    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-    dft4<DIR>(e0, e1, e2, e3);
-    dft4<DIR>(o0, o1, o2, o3);
-    o1 = mul_w16<DIR, 2>(o1);
-    o2 = mul_w16<DIR, 4>(o2);
-    o3 = mul_w16<DIR, 6>(o3);
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, o1);
-    v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2);
-    v[6] = csub(e2, o2);
-    v[3] = cadd(e3, o3);
-    v[7] = csub(e3, o3);
-  } else if constexpr (R == 32) {
-    // 32 = 2 x 16: X[m] = E[m] + w32^m O[m], X[m + 16] = E[m] - w32^m O[m]
-    constexpr float c32[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
-                              0.83146961230254523708f, 0.70710678118654752440f, 0.55557023301960222474f,
-                              0.38268343236508977173f, 0.19509032201612826785f, 0.0f};
-    float2 e[16], o[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      e[i] = v[2 * i];
-      o[i] = v[2 * i + 1];
-    }
-    dft<16, DIR>(e);
-    dft<16, DIR>(o);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      // w32^m = cos(pi m/16) + DIR i sin(pi m/16)
-      const float c = m <= 8 ? c32[m] : -c32[16 - m];
-      const float sn = m <= 8 ? c32[8 - m] : c32[m - 8];
-      const float sd = DIR > 0 ? sn : -sn;
-      const float2 t = make_float2(o[m].x * c - o[m].y * sd, o[m].x * sd + o[m].y * c);
-      v[m] = cadd(e[m], t);
-      v[m + 16] = csub(e[m], t);
-    }
-  } else {
-    static_assert(R == 16, "radix");
-    // 16 = 4 x 4: inputs r1 + 4 r2, outputs m2 + 4 m1
-    float2 y[16];
-#pragma unroll
-    for (int r1 = 0; r1 < 4; ++r1) {
-      float2 a = v[r1], b = v[r1 + 4], c = v[r1 + 8], d = v[r1 + 12];
-      dft4<DIR>(a, b, c, d);
-      y[r1 * 4 + 0] = a;
-      y[r1 * 4 + 1] = b;
-      y[r1 * 4 + 2] = c;
-      y[r1 * 4 + 3] = d;
-    }
-    y[5] = mul_w16<DIR, 1>(y[5]);
-    y[6] = mul_w16<DIR, 2>(y[6]);
-    y[7] = mul_w16<DIR, 3>(y[7]);
-    y[9] = mul_w16<DIR, 2>(y[9]);
-    y[10] = mul_w16<DIR, 4>(y[10]);
-    y[11] = mul_w16<DIR, 6>(y[11]);
-    y[13] = mul_w16<DIR, 3>(y[13]);
-    y[14] = mul_w16<DIR, 6>(y[14]);
-    y[15] = mul_w16<DIR, 9>(y[15]);
-#pragma unroll
-    for (int m2 = 0; m2 < 4; ++m2) {
-      float2 a = y[0 * 4 + m2], b = y[1 * 4 + m2], c = y[2 * 4 + m2], d = y[3 * 4 + m2];
-      dft4<DIR>(a, b, c, d);
-      v[m2 + 0] = a;
-      v[m2 + 4] = b;
-      v[m2 + 8] = c;
-      v[m2 + 12] = d;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------
-// Stockham stage schedule for a length-L line with EPT elements per thread
-// ---------------------------------------------------------------------------------
-constexpr int stage_radix(int L, int ept, int s) {
-  int rem = L;
-  for (int i = 0; i < s; ++i) rem /= (rem < ept ? rem : ept);
-  return rem < ept ? rem : ept;
-}
-constexpr int stage_ns(int L, int ept, int s) {  // product of the radices before stage s
-  int ns = 1;
-  for (int i = 0; i < s; ++i) ns *= stage_radix(L, ept, i);
-  return ns;
-}
-constexpr int num_stages(int L, int ept) {
-  int n = 0, rem = L;
-  while (rem > 1) {
-    rem /= (rem < ept ? rem : ept);
-    ++n;
-  }
-  return n;
-}
-
-// exp(dir 2 pi i idx / N) from a half-wave table T[m] = exp(2 pi i m / N), m < N/2
-// (64 KB at N = 16384); exp(2 pi i (m + N/2) / N) = -T[m].
-struct Tw {
-  const float2 *t;
-  int hmask;  // N/2 - 1
-  int hbit;   // N/2
-};
-
-__device__ __forceinline__ float2 twiddle(const Tw &tw, int idx, int dir) {
-  float2 w = __ldg(tw.t + (idx & tw.hmask));
-  if (idx & tw.hbit) w = make_float2(-w.x, -w.y);
-  if (dir < 0) w.y = -w.y;
-  return w;
-}
-
-// Butterfly b of this thread has index j = jt + b * TPL (< L/R); its inputs sit at
-// j + r L/R and, after the twiddles w_{NS R}^{(j mod NS) r} and the radix-R DFT, its
-// outputs belong at (j / NS) NS R + (j mod NS) + r NS.
-template <int L, int EPT, int TPL, int S, int DIR>
-__device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const Tw &tw, int twscale) {
-  constexpr int R = stage_radix(L, EPT, S);
-  constexpr int NS = stage_ns(L, EPT, S);
-#pragma unroll
-  for (int b = 0; b < EPT / R; ++b) {
-    const int j = jt + b * TPL;
-    if constexpr (NS > 1) {
-      const int k = j % NS;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const int m = k * r * (L / (NS * R));
-        v[b * R + r] = cmul(v[b * R + r], twiddle(tw, m * twscale, DIR));
-      }
-    }
-    dft<R, DIR>(&v[b * R]);
-  }
-}
-
-template <int L, int EPT, int TPL, int S>
-__device__ __forceinline__ int in_index(int jt, int b, int r) {
-  constexpr int R = stage_radix(L, EPT, S);
-  return jt + b * TPL + r * (L / R);
-}
-template <int L, int EPT, int TPL, int S>
-__device__ __forceinline__ int out_index(int jt, int b, int r) {
-  constexpr int R = stage_radix(L, EPT, S);
-  constexpr int NS = stage_ns(L, EPT, S);
-  const int j = jt + b * TPL;
-  return (j / NS) * NS * R + (j % NS) + r * NS;
-}
-
-// Run stages 1 .. last-1 through shared memory; `smi` maps a line index to a shared
-// memory slot.  On entry v holds the outputs of stage 0 (not yet stored); on return v
-// holds the inputs of the last stage, already loaded.
-template <int L, int EPT, int TPL, int S, int DIR, class SMI>
-__device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *sm, SMI smi,
-                                              const Tw &tw, int twscale) {
-  constexpr int NST = num_stages(L, EPT);
-  if constexpr (S < NST) {
-    // store outputs of stage S-1
-    constexpr int RP = stage_radix(L, EPT, S - 1);
-#pragma unroll
-    for (int b = 0; b < EPT / RP; ++b)
-#pragma unroll
-      for (int r = 0; r < RP; ++r) sm[smi(out_index<L, EPT, TPL, S - 1>(jt, b, r))] = v[b * RP + r];
-    __syncthreads();
-    constexpr int R = stage_radix(L, EPT, S);
-#pragma unroll
-    for (int b = 0; b < EPT / R; ++b)
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = sm[smi(in_index<L, EPT, TPL, S>(jt, b, r))];
-    if constexpr (S + 1 < NST) {
-      __syncthreads();  // every load of this stage done before the next stores
-      stage_compute<L, EPT, TPL, S, DIR>(v, jt, tw, twscale);
-      middle_stages<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, tw, twscale);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------------
-// pass R: row FFTs
-// ---------------------------------------------------------------------------------
-template <int N>
-struct RowCfg {
-  // 32 elements per thread for the longest rows: radix 32, 32, 16 (two shared-memory
-  // round trips); 16 otherwise.  Rows are padded by one element every EPT elements.
-  static constexpr int EPT = N >= 16384 ? 32 : (N >= 16 ? 16 : N);
-  static constexpr int TPR = N / EPT;
-  static constexpr int RPC = TPR >= 256 ? 1 : 256 / TPR;
-  static constexpr int THREADS = TPR * RPC;
-  static constexpr int PADL = N + N / EPT;
-};
 
 template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
@@ -436,7 +199,7 @@ struct ColCfg {
 
 template <int LB, int DIR, bool TW_FIRST>
 __global__ void __launch_bounds__(ColCfg<LB>::THREADS)
-k_cols_a(float2 *__restrict__ planes, Tw tw, int n) {
+k_cols_a(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ) {
   using C = ColCfg<LB>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LB, EPT);
@@ -456,7 +219,9 @@ k_cols_a(float2 *__restrict__ planes, Tw tw, int n) {
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int i = in_index<LB, EPT, TPL, 0>(jt, b, r);
-      float2 x = base[(size_t)i * rstride];
+      // rows the gridder left empty are zero: do not read them
+      float2 x = (occ && !occ[(size_t)blockIdx.z * n + a + A * i]) ? make_float2(0.0f, 0.0f)
+                                                                     : base[(size_t)i * rstride];
       if (TW_FIRST) x = cmul(x, twiddle(tw, a * i, DIR));
       v[b * R0 + r] = x;
     }
@@ -812,29 +577,30 @@ cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool p
 }
 
 template <int LB, int DIR, bool TWF>
-static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes) {
+static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes, const uint8_t *occ) {
   dim3 grd(p->n / kCB, p->n / LB, nplanes);
-  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n);
+  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ);
   return cudaGetLastError();
 }
 
 template <int DIR, bool TWF>
-static cudaError_t cols_a_dispatch(wst_plan_s *p, float2 *planes, int nplanes) {
+static cudaError_t cols_a_dispatch(wst_plan_s *p, float2 *planes, int nplanes, const uint8_t *occ) {
   switch (p->fb) {
-    case 8: return launch_cols_a<8, DIR, TWF>(p, planes, nplanes);
-    case 16: return launch_cols_a<16, DIR, TWF>(p, planes, nplanes);
-    case 32: return launch_cols_a<32, DIR, TWF>(p, planes, nplanes);
-    case 64: return launch_cols_a<64, DIR, TWF>(p, planes, nplanes);
-    case 128: return launch_cols_a<128, DIR, TWF>(p, planes, nplanes);
+    case 8: return launch_cols_a<8, DIR, TWF>(p, planes, nplanes, occ);
+    case 16: return launch_cols_a<16, DIR, TWF>(p, planes, nplanes, occ);
+    case 32: return launch_cols_a<32, DIR, TWF>(p, planes, nplanes, occ);
+    case 64: return launch_cols_a<64, DIR, TWF>(p, planes, nplanes, occ);
+    case 128: return launch_cols_a<128, DIR, TWF>(p, planes, nplanes, occ);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first) {
+cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first,
+                       const uint8_t *occ) {
   if (nplanes <= 0) return cudaSuccess;
   p->launches += 1;
-  if (dir > 0 && !twiddle_first) return cols_a_dispatch<1, false>(p, planes, nplanes);
-  if (dir < 0 && twiddle_first) return cols_a_dispatch<-1, true>(p, planes, nplanes);
+  if (dir > 0 && !twiddle_first) return cols_a_dispatch<1, false>(p, planes, nplanes, occ);
+  if (dir < 0 && twiddle_first) return cols_a_dispatch<-1, true>(p, planes, nplanes, occ);
   return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,368 @@
+// Row-wise gridding fused with the row FFT (K-G + K-F rows), and its adjoint fused with
+// degridding (K-D) or with the tabulated-kernel gradient (K-KG).
+//
+// Forward, per (plane, row q) work item: the visibilities whose W-row footprint covers
+// row q are the contiguous buckets j0 = q - W + 1 ... q (k_sort.cu).  If there are
+// none the row is zero: the item writes zeros and is done (no gridding, no FFT, no read
+// of a plane).  Otherwise the row is accumulated in shared memory -- each thread takes
+// visibilities, weights its W taps by G(a - W/2 + g_x) G(d - W/2 + g_y), d = q - j0,
+// and adds them with shared-memory atomics (section 2, Eq. 3) -- then transformed in
+// place (centring sign (-1)^(p+q) folded into the first stage) and written once.  The
+// paper's gridder instead adds every tap of every visibility to the mesh in global
+// memory, and the FFT reads the mesh back.
+//
+// Adjoint, per item: the row of the adjoint plane is transformed with the negative
+// exponent (sign (-1)^(p+q) after the last stage), kept in shared memory, and every
+// visibility whose footprint covers the row reads its W taps from it: degridding adds
+// w G_y(d) sum_a G_x(a) row[i0 + a] to dvis; the kernel gradient scatters the tap
+// products into a shared partial table.  Rows nobody reads are skipped.
+//
+// Items are handed out by a device counter to persistent CTAs (one row or, for short
+// rows, RowCfg::RPC rows per CTA step).
+#include "fft_core.cuh"
+
+namespace wst {
+
+template <int N>
+__device__ __forceinline__ void zero_row(float2 *srow, int jt) {
+  float4 *p = reinterpret_cast<float4 *>(srow);
+  for (int i = jt; i < N / 2; i += RowCfg<N>::TPR) p[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// Accumulate the visibilities of rows j0 = q - d_lo ... q into the row, stored planar
+// (re[0..N), im[0..N)).  Their sub-buckets are contiguous in the sorted records, so the
+// range bnd[0] .. bnd[d_lo + 1] is split evenly over the row's threads, one visibility
+// per thread; bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0 fixes the support at
+// compile time.
+template <int N, int WT>
+__device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *__restrict__ rec,
+                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt) {
+  constexpr int TPR = RowCfg<N>::TPR;
+  const int W = WT > 0 ? WT : kp.support;
+  const uint32_t s_end = bnd[d_lo + 1];
+  for (uint32_t s = bnd[0] + jt; s < s_end; s += TPR) {
+    int i = d_lo;
+    while (s < bnd[i]) --i;  // the last row starting at or before s
+    const Record r = rec[s];
+    const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
+    const float gx = rec_gx(r);
+    const int i0 = rec_i0(r);
+    if constexpr (WT > 0) {
+#pragma unroll
+      for (int a = 0; a < WT; ++a) {
+        const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
+        atomicAdd(&sre[i0 + a], r.vre * g);
+        atomicAdd(&sim[i0 + a], r.vim * g);
+      }
+    } else {
+      for (int a = 0; a < W; ++a) {
+        const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
+        atomicAdd(&sre[i0 + a], r.vre * g);
+        atomicAdd(&sim[i0 + a], r.vim * g);
+      }
+    }
+  }
+}
+
+template <int N, bool FFT, int WT>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS)
+k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int np,
+            KernelParams kp, float2 *__restrict__ out, uint8_t *__restrict__ occ,
+            unsigned long long *__restrict__ counter, Tw tw) {
+  using C = RowCfg<N>;
+  constexpr int EPT = C::EPT, TPR = C::TPR, RPC = C::RPC;
+  constexpr int NST = num_stages(N, EPT);
+  constexpr int R0 = stage_radix(N, EPT, 0);
+  constexpr int RL = stage_radix(N, EPT, NST - 1);
+  extern __shared__ __align__(16) float2 sm_rows[];
+  __shared__ long long s_item;
+  __shared__ uint32_t s_bnd[RPC][kMaxSupport + 2];
+  const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
+  float2 *srow = sm_rows + rl * C::PADL;
+  auto smi = [](int i) { return i + i / EPT; };
+  const long long total = (long long)np * N;
+  const int W = WT > 0 ? WT : kp.support;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)RPC);
+    __syncthreads();
+    const long long base = s_item;
+    __syncthreads();
+    if (base >= total) break;
+    const long long item = base + rl;
+    const bool valid = item < total;
+    const int pl = valid ? (int)(item / N) : 0;
+    const int q = valid ? (int)(item % N) : 0;
+    const int64_t b0 = (int64_t)(p0 + pl) * N;
+    const bool empty = !valid || off[(b0 + max(0, q - W + 1)) * kColBlocks] == off[(b0 + q + 1) * kColBlocks];
+    float2 *orow = out + ((int64_t)pl * N + q) * N;
+    if (valid && jt == 0) occ[(int64_t)pl * N + q] = empty ? 0 : 1;
+    if constexpr (RPC == 1) {
+      if (empty) {  // uniform across the CTA: one row per step
+        float4 *o4 = reinterpret_cast<float4 *>(orow);
+        for (int i = jt; i < N / 2; i += TPR) o4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        continue;
+      }
+    }
+    float *sre = reinterpret_cast<float *>(srow), *sim = sre + N;  // planar accumulation
+    const int d_lo = min(q, W - 1);
+    if (!empty)
+      for (int i = jt; i <= d_lo + 1; i += TPR) s_bnd[rl][i] = off[(b0 + q - d_lo + i) * kColBlocks];
+    zero_row<N>(srow, jt);
+    __syncthreads();
+    if (!empty) grid_row<N, WT>(sre, sim, rec, s_bnd[rl], d_lo, kp, jt);
+    __syncthreads();
+    if constexpr (FFT) {
+      float2 v[EPT];
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+          const float sg = ((idx + q) & 1) ? -1.0f : 1.0f;  // centring sign
+          v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
+        }
+      __syncthreads();  // natural-order reads done before the padded writes
+      stage_compute<N, EPT, TPR, 0, 1>(v, jt, tw, 1);
+      middle_stages<N, EPT, TPR, 1, 1>(v, jt, srow, smi, tw, 1);
+      stage_compute<N, EPT, TPR, NST - 1, 1>(v, jt, tw, 1);
+      if (valid) {
+#pragma unroll
+        for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)] = v[b * RL + r];
+      }
+    } else {
+      if (valid)
+        for (int i = jt; i < N; i += TPR) orow[i] = make_float2(sre[i], sim[i]);
+    }
+    __syncthreads();  // the row buffer is reused by the next step
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// adjoint: row FFT^H of the adjoint plane + degridding / kernel gradient
+// -------------------------------------------------------------------------------------
+template <int N, bool KGRAD>
+__global__ void __launch_bounds__(RowCfg<N>::THREADS)
+k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec,
+               const uint32_t *__restrict__ off, const uint32_t *__restrict__ perm,
+               const float *__restrict__ rweight, int p0, int np, KernelParams kp,
+               float2 *__restrict__ dvis, float *__restrict__ dtab,
+               unsigned long long *__restrict__ counter, Tw tw) {
+  using C = RowCfg<N>;
+  constexpr int EPT = C::EPT, TPR = C::TPR, RPC = C::RPC;
+  constexpr int NST = num_stages(N, EPT);
+  constexpr int R0 = stage_radix(N, EPT, 0);
+  constexpr int RL = stage_radix(N, EPT, NST - 1);
+  extern __shared__ __align__(16) float2 sm_rows[];
+  __shared__ long long s_item;
+  float *ptab = reinterpret_cast<float *>(sm_rows + RPC * C::PADL);  // KGRAD partial table
+  const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
+  float2 *srow = sm_rows + rl * C::PADL;
+  auto smi = [](int i) { return i + i / EPT; };
+  const long long total = (long long)np * N;
+  const int W = kp.support;
+  if (KGRAD) {
+    for (int i = threadIdx.x; i < kp.table_len; i += blockDim.x) ptab[i] = 0.0f;
+  }
+  while (true) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)RPC);
+    __syncthreads();
+    const long long base = s_item;
+    __syncthreads();
+    if (base >= total) break;
+    const long long item = base + rl;
+    const bool valid = item < total;
+    const int pl = valid ? (int)(item / N) : 0;
+    const int q = valid ? (int)(item % N) : 0;
+    const int64_t b0 = (int64_t)(p0 + pl) * N;
+    const bool empty = !valid || off[(b0 + max(0, q - W + 1)) * kColBlocks] == off[(b0 + q + 1) * kColBlocks];
+    if constexpr (RPC == 1) {
+      if (empty) continue;  // nobody reads this row
+    }
+    const float2 *grow = planes + ((int64_t)pl * N + q) * N;
+    float2 v[EPT];
+#pragma unroll
+    for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[b * R0 + r] = grow[in_index<N, EPT, TPR, 0>(jt, b, r)];
+    stage_compute<N, EPT, TPR, 0, -1>(v, jt, tw, 1);
+    middle_stages<N, EPT, TPR, 1, -1>(v, jt, srow, smi, tw, 1);
+    stage_compute<N, EPT, TPR, NST - 1, -1>(v, jt, tw, 1);
+    __syncthreads();  // every padded read done before the natural-order writes
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int idx = out_index<N, EPT, TPR, NST - 1>(jt, b, r);
+        float2 x = v[b * RL + r];
+        if ((idx + q) & 1) x = make_float2(-x.x, -x.y);
+        srow[idx] = x;
+      }
+    __syncthreads();
+    if (valid && !empty) {
+      for (int d = 0; d < W && q - d >= 0; ++d) {
+        const uint32_t s0 = off[(b0 + q - d) * kColBlocks], s1 = off[(b0 + q - d + 1) * kColBlocks];
+        const float ty = (float)d - kp.half;
+        for (uint32_t s = s0 + jt; s < s1; s += TPR) {
+          const Record rc = rec[s];
+          const float targ_y = ty + rec_gy(rc);
+          const float gy = kernel_eval(kp, targ_y);
+          const float gx0 = rec_gx(rc);
+          const float2 *cell = srow + rec_i0(rc);
+          if (!KGRAD) {
+            float are = 0.0f, aim = 0.0f;
+            for (int a = 0; a < W; ++a) {
+              const float g = kernel_eval(kp, (float)a - kp.half + gx0);
+              are = fmaf(g, cell[a].x, are);
+              aim = fmaf(g, cell[a].y, aim);
+            }
+            const float wt = (rweight ? rweight[s] : 1.0f) * gy;
+            const uint32_t j = perm[s];
+            atomicAdd(&dvis[j].x, wt * are);
+            atomicAdd(&dvis[j].y, wt * aim);
+          } else {
+            // c_a = Re(conj(gh[q, i0 + a]) (w V)); x-profile tap a gets c_a G_y(d), the
+            // y-profile tap d gets sum_a c_a G_x(a); each is split over the two table
+            // samples bracketing the tap's argument
+            float sum_cx = 0.0f;
+            for (int a = 0; a < W; ++a) {
+              const float targ = (float)a - kp.half + gx0;
+              const float2 c = cell[a];
+              const float cr = c.x * rc.vre + c.y * rc.vim;
+              sum_cx = fmaf(cr, kernel_eval(kp, targ), sum_cx);
+              const float pos = (targ + kp.half) * kp.table_scale;
+              int i = (int)floorf(pos);
+              i = max(0, min(i, kp.table_len - 2));
+              const float f = pos - (float)i;
+              atomicAdd(&ptab[i], cr * gy * (1.0f - f));
+              atomicAdd(&ptab[i + 1], cr * gy * f);
+            }
+            const float pos = (targ_y + kp.half) * kp.table_scale;
+            int i = (int)floorf(pos);
+            i = max(0, min(i, kp.table_len - 2));
+            const float f = pos - (float)i;
+            atomicAdd(&ptab[i], sum_cx * (1.0f - f));
+            atomicAdd(&ptab[i + 1], sum_cx * f);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (KGRAD) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kp.table_len; i += blockDim.x)
+      if (ptab[i] != 0.0f) atomicAdd(&dtab[i], ptab[i]);
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// host side
+// -------------------------------------------------------------------------------------
+static Tw tw_half(const wst_plan_s *p) {
+  Tw t;
+  t.t = p->tw;
+  t.hmask = (p->n >> 1) - 1;
+  t.hbit = p->n >> 1;
+  return t;
+}
+
+template <class K>
+static cudaError_t persistent_grid(wst_plan_s *p, K kern, int threads, size_t smem, int &grid) {
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) return e;
+  grid = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
+}
+
+template <int N, bool FFT>
+static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) {
+  using C = RowCfg<N>;
+  // the imaging path has the common supports unrolled
+  auto kern = !FFT ? k_grid_rows<N, FFT, 0>
+              : p->cfg.support == 7 ? k_grid_rows<N, FFT, 7>
+              : p->cfg.support == 8 ? k_grid_rows<N, FFT, 8> : k_grid_rows<N, FFT, 0>;
+  const size_t smem = sizeof(float2) * C::RPC * C::PADL;
+  int grid = 0;
+  cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
+  if (e != cudaSuccess) return e;
+  unsigned long long *counter = p->W_.counters + CNT_WORK;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, C::THREADS, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, np, kernel_params(p), out,
+                                             p->W_.occ, counter, tw_half(p));
+  return cudaGetLastError();
+}
+
+template <int N, bool KGRAD>
+static cudaError_t launch_rows_adjoint(wst_plan_s *p, int p0, int np, const float2 *planes, float2 *dvis,
+                                       float *dtab) {
+  using C = RowCfg<N>;
+  auto kern = k_rows_adjoint<N, KGRAD>;
+  const size_t smem = sizeof(float2) * C::RPC * C::PADL + (KGRAD ? sizeof(float) * p->cfg.ktable_len : 0);
+  int grid = 0;
+  cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
+  if (e != cudaSuccess) return e;
+  unsigned long long *counter = p->W_.counters + CNT_WORK;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, C::THREADS, smem, p->stream>>>(planes, p->W_.records, p->W_.offsets, p->W_.perm,
+                                             p->has_weight ? p->W_.rweight : nullptr, p0, np, kernel_params(p),
+                                             dvis, dtab, counter, tw_half(p));
+  return cudaGetLastError();
+}
+
+#define WST_N_SWITCH(n, CALL)         \
+  switch (n) {                        \
+    case 64: return CALL(64);         \
+    case 128: return CALL(128);       \
+    case 256: return CALL(256);       \
+    case 512: return CALL(512);       \
+    case 1024: return CALL(1024);     \
+    case 2048: return CALL(2048);     \
+    case 4096: return CALL(4096);     \
+    case 8192: return CALL(8192);     \
+    case 16384: return CALL(16384);   \
+  }                                   \
+  return cudaErrorInvalidValue;
+
+cudaError_t grid_rows(wst_plan_s *p, int p0, int p1, float2 *out, bool fft) {
+  const int np = p1 - p0;
+  if (np <= 0) return cudaSuccess;
+  p->launches += 1;
+  if (fft) {
+#define CALL_F(n) launch_grid_rows<n, true>(p, p0, np, out)
+    WST_N_SWITCH(p->n, CALL_F)
+#undef CALL_F
+  } else {
+#define CALL_G(n) launch_grid_rows<n, false>(p, p0, np, out)
+    WST_N_SWITCH(p->n, CALL_G)
+#undef CALL_G
+  }
+}
+
+cudaError_t rows_adjoint(wst_plan_s *p, int p0, int p1, const float2 *planes, float2 *dvis, float *dtab) {
+  const int np = p1 - p0;
+  if (np <= 0) return cudaSuccess;
+  p->launches += 1;
+  if (dtab) {
+#define CALL_K(n) launch_rows_adjoint<n, true>(p, p0, np, planes, nullptr, dtab)
+    WST_N_SWITCH(p->n, CALL_K)
+#undef CALL_K
+  } else {
+#define CALL_D(n) launch_rows_adjoint<n, false>(p, p0, np, planes, dvis, nullptr)
+    WST_N_SWITCH(p->n, CALL_D)
+#undef CALL_D
+  }
+}
+
+}  // namespace wst

@@ -1,18 +1,15 @@
-// K-S: device bucket sort of visibilities by (image, w-plane, 64x64 tile, spill class).
+// K-S: device bucket sort of visibilities by (image, w-plane, row of the first tap).
 //
 // Placement follows section 2 / Eq. 3: a visibility at x = N/2 + u FoV touches the W
 // cells i0 = ceil(x - W/2) ... i0 + W - 1 and goes to the closest w-plane.  x, the tap
 // start and the plane index are computed in FP64 with explicitly rounded operations
 // (no contraction), so they are the same numbers a plain double-precision program
-// gets.  The sub-cell offset g = i0 - (x - W/2) in [0,1) is then quantised to 24 bits.
+// gets.  The sub-cell offsets g = i0 - (x - W/2) in [0,1) are quantised to 24 bits.
 //
-// Buckets replace the paper's per-slab linked lists (section 3.2): both exist to give
-// the gridding kernel contiguous visibilities for one region of the mesh.  A record
-// is filed under the tile that holds its tap start; the spill class says whether its
-// footprint crosses into the right (x) and/or lower (y) neighbour tile, so that a tile
-// owner can read exactly the neighbour records that reach into it:
-//   class 0: none, 1: x only, 2: x and y, 3: y only
-// (left neighbour needs classes 1..2, upper neighbour 2..3, upper-left neighbour 2).
+// Buckets replace the paper's per-slab linked lists (section 3.2): both hand the
+// gridder the visibilities of one region of the mesh contiguously.  Here the region
+// is one row j0 of one plane, so grid row q of a plane reads the W contiguous buckets
+// j0 = q - W + 1 ... q as one range.
 #include "wst_internal.cuh"
 
 namespace wst {
@@ -54,7 +51,7 @@ __global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax)
 }
 
 struct SortGeom {
-  int n, W, tiles, n_w;
+  int n, W, n_w;
   double half_n, half_w, fov;
 };
 
@@ -100,15 +97,11 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
           const int i0 = (int)ci, j0 = (int)cj;
           // exact offsets in [0, 1), quantised to 2^-24 (round to nearest, kept below 1)
           const double gx = __dsub_rn(ci, hx), gy = __dsub_rn(cj, hy);
-          uint32_t fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
-          uint32_t fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
-          const int tx = i0 >> kLogTile, ty = j0 >> kLogTile;
-          const int cx = i0 & (kTile - 1), cy = j0 & (kTile - 1);
-          const bool sx = cx > kTile - g.W, sy = cy > kTile - g.W;
-          const int cls = sx ? (sy ? 2 : 1) : (sy ? 3 : 0);
-          key = (uint32_t)(((((int64_t)img * g.n_w + k) * g.tiles + ty) * g.tiles + tx) * kClasses + cls);
-          xpack = ((uint32_t)cx << kFracBits) | fx;
-          ypack = ((uint32_t)cy << kFracBits) | fy;
+          const uint32_t fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
+          const uint32_t fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
+          key = (uint32_t)((((int64_t)img * g.n_w + k) * g.n + j0) * kColBlocks + (int64_t)i0 * kColBlocks / g.n);
+          xpack = ((uint32_t)i0 << 18) | (fx >> 6);
+          ypack = ((fx & 63u) << 24) | fy;
           kept = true;
         }
       }
@@ -279,7 +272,6 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   SortGeom g;
   g.n = p->n;
   g.W = p->W;
-  g.tiles = p->tiles;
   g.n_w = p->n_w;
   g.half_n = 0.5 * p->n;
   g.half_w = 0.5 * p->W;
@@ -300,7 +292,7 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
 // per-visibility placement read back from the sorted records (inspection call)
 // ---------------------------------------------------------------------------------
 __global__ void k_vis_cells(const Record *rec, const uint32_t *perm, const uint32_t *offsets,
-                            int64_t n_buckets, int64_t n_bound, int tiles, int n_w,
+                            int64_t n_buckets, int64_t n_bound, int n, int n_w,
                             int32_t *plane, int32_t *i0, int32_t *j0) {
   const int64_t n_kept = offsets[n_buckets];  // records beyond it are not written
   const int64_t n_iter = n_kept < n_bound ? n_kept : n_bound;
@@ -312,15 +304,11 @@ __global__ void k_vis_cells(const Record *rec, const uint32_t *perm, const uint3
       int64_t mid = (lo + hi) >> 1;
       if (offsets[mid] <= (uint32_t)s) lo = mid; else hi = mid;
     }
-    const int64_t key = lo / kClasses;
-    const int tx = (int)(key % tiles);
-    const int ty = (int)((key / tiles) % tiles);
-    const int k = (int)((key / ((int64_t)tiles * tiles)) % n_w);
-    const Record r = rec[s];
     const uint32_t j = perm[s];
-    plane[j] = k;
-    i0[j] = tx * kTile + (int)(r.xpack >> kFracBits);
-    j0[j] = ty * kTile + (int)(r.ypack >> kFracBits);
+    const int64_t row_bucket = lo / kColBlocks;
+    plane[j] = (int)((row_bucket / n) % n_w);
+    j0[j] = (int)(row_bucket % n);
+    i0[j] = rec_i0(rec[s]);
   }
 }
 
@@ -332,7 +320,7 @@ cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, i
   if ((e = cudaMemsetAsync(j0, 0xFF, sizeof(int32_t) * p->n_vis, s))) return e;
   if (n_bound > 0)
     k_vis_cells<<<grid_for(n_bound, 256, 152 * 16), 256, 0, s>>>(
-        p->W_.records, p->W_.perm, p->W_.offsets, p->n_buckets, n_bound, p->tiles, p->n_w, plane,
+        p->W_.records, p->W_.perm, p->W_.offsets, p->n_buckets, n_bound, p->n, p->n_w, plane,
         i0, j0);
   p->launches += 1;
   return cudaGetLastError();

@@ -43,7 +43,7 @@ int ilog2(int x) {
 }
 
 struct Layout {
-  size_t keyinfo_planes, records, perm, rweight, offsets, scan_tmp, counters, wminmax, comp, total;
+  size_t keyinfo_planes, records, perm, rweight, offsets, scan_tmp, counters, wminmax, occ, comp, total;
 };
 
 Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
@@ -67,6 +67,8 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   off += align_up(CNT_SLOTS * sizeof(unsigned long long));
   L.wminmax = off;
   off += align_up((size_t)2 * p->batch * sizeof(uint32_t));
+  L.occ = off;
+  off += align_up((size_t)p->n_planes * p->n);
   L.comp = off;
   if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n * p->n * sizeof(float2));
   L.total = off;
@@ -159,8 +161,7 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   }
   if (c.batch < 1 || c.batch > 4096 || c.planes_per_chunk < 0) return WST_ERR_INVALID_ARG;
   if (c.flags & ~(WST_FLAG_KAHAN | WST_FLAG_FP64_SCREEN | WST_FLAG_TIMING)) return WST_ERR_INVALID_ARG;
-  const int64_t tiles = c.n / kTile;
-  const int64_t n_buckets = (int64_t)c.batch * c.n_w * tiles * tiles * kClasses;
+  const int64_t n_buckets = (int64_t)c.batch * c.n_w * c.n * kColBlocks;
   if (n_buckets + 1 >= (int64_t)0xFFFFFFFFu) return WST_ERR_UNSUPPORTED;
 
   wst_plan_s *p = new wst_plan_s();
@@ -170,7 +171,6 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   p->n = c.n;
   p->log2n = ilog2(c.n);
   p->W = c.support;
-  p->tiles = (int)tiles;
   p->n_w = c.n_w;
   p->batch = c.batch;
   p->n_planes = c.batch * c.n_w;
@@ -282,6 +282,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.scan_tmp = (uint32_t *)(p->ws + L.scan_tmp);
   W.counters = (unsigned long long *)(p->ws + L.counters);
   W.wminmax = (uint32_t *)(p->ws + L.wminmax);
+  W.occ = (uint8_t *)(p->ws + L.occ);
   W.comp = (p->chunk < p->n_planes) ? (float2 *)(p->ws + L.comp) : nullptr;
   W.bytes = L.total;
   p->launches = 0;
@@ -313,7 +314,7 @@ wst_status wst_grid(wst_plan p, int32_t b, int32_t e, void *out) {
   wst_status st = check_ready(p);
   if (st) return st;
   if (b < 0 || e > p->n_planes || b > e || (!out && e > b)) return fail(p, WST_ERR_INVALID_ARG, "plane range or output");
-  WST_CUDA(p, grid_planes(p, b, e, (float2 *)out, false), "grid");
+  WST_CUDA(p, grid_rows(p, b, e, (float2 *)out, false), "grid");
   return WST_OK;
 }
 
@@ -325,7 +326,7 @@ wst_status wst_fft_correct(wst_plan p, int32_t b, int32_t e, void *grid_inout, v
   if (!grid_inout || !image_inout) return fail(p, WST_ERR_INVALID_ARG, "NULL buffer");
   float2 *g = (float2 *)grid_inout;
   WST_CUDA(p, fft_rows(p, g, e - b, +1, true, false), "rows");
-  WST_CUDA(p, fft_cols_a(p, g, e - b, +1, false), "cols A");
+  WST_CUDA(p, fft_cols_a(p, g, e - b, +1, false, nullptr), "cols A");
   WST_CUDA(p, fft_cols_b_accumulate(p, g, b, e, (float2 *)image_inout, nullptr,
                                     (p->cfg.flags & WST_FLAG_KAHAN) != 0, false, true),
            "cols B");
@@ -354,13 +355,10 @@ wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
   for (int p0 = 0; p0 < p->n_planes; p0 += p->chunk) {
     const int p1 = (p0 + p->chunk < p->n_planes) ? p0 + p->chunk : p->n_planes;
     WST_CUDA(p, time_begin(p, p->ev_img, ST_GRID), "event");
-    WST_CUDA(p, grid_planes(p, p0, p1, planes, true), "grid");
-    WST_CUDA(p, time_end(p, p->ev_img), "event");
-    WST_CUDA(p, time_begin(p, p->ev_img, ST_ROWS), "event");
-    WST_CUDA(p, fft_rows(p, planes, p1 - p0, +1, false, false), "rows");
+    WST_CUDA(p, grid_rows(p, p0, p1, planes, true), "grid + rows");
     WST_CUDA(p, time_end(p, p->ev_img), "event");
     WST_CUDA(p, time_begin(p, p->ev_img, ST_COLS_A), "event");
-    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, +1, false), "cols A");
+    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, +1, false, p->W_.occ), "cols A");
     WST_CUDA(p, time_end(p, p->ev_img), "event");
     WST_CUDA(p, time_begin(p, p->ev_img, ST_COLS_B), "event");
     WST_CUDA(p, fft_cols_b_accumulate(p, planes, p0, p1, img, p->W_.comp, kahan, correct, false), "cols B");
@@ -382,9 +380,8 @@ wst_status wst_degrid(wst_plan p, const void *dimage, void *dvis, uint32_t flags
   for (int p0 = 0; p0 < p->n_planes; p0 += p->chunk) {
     const int p1 = (p0 + p->chunk < p->n_planes) ? p0 + p->chunk : p->n_planes;
     WST_CUDA(p, fft_cols_bh_from_image(p, (const float2 *)dimage, p0, p1, planes, correct), "cols B^H");
-    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, -1, true), "cols A^H");
-    WST_CUDA(p, fft_rows(p, planes, p1 - p0, -1, false, true), "rows^H");
-    WST_CUDA(p, degrid_planes(p, p0, p1, planes, (float2 *)dvis), "degrid");
+    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, -1, true, nullptr), "cols A^H");
+    WST_CUDA(p, rows_adjoint(p, p0, p1, planes, (float2 *)dvis, nullptr), "rows^H + degrid");
   }
   return WST_OK;
 }
@@ -401,9 +398,8 @@ wst_status wst_kernel_grad(wst_plan p, const void *dimage, float *dtable, uint32
   for (int p0 = 0; p0 < p->n_planes; p0 += p->chunk) {
     const int p1 = (p0 + p->chunk < p->n_planes) ? p0 + p->chunk : p->n_planes;
     WST_CUDA(p, fft_cols_bh_from_image(p, (const float2 *)dimage, p0, p1, planes, false), "cols B^H");
-    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, -1, true), "cols A^H");
-    WST_CUDA(p, fft_rows(p, planes, p1 - p0, -1, false, true), "rows^H");
-    WST_CUDA(p, kernel_grad_planes(p, p0, p1, planes, dtable), "kernel grad");
+    WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, -1, true, nullptr), "cols A^H");
+    WST_CUDA(p, rows_adjoint(p, p0, p1, planes, nullptr, dtable), "rows^H + kernel gradient");
   }
   return WST_OK;
 }

@@ -11,24 +11,32 @@
 
 namespace wst {
 
-constexpr int kTile = 64;        // gridding tile side (cells)
-constexpr int kLogTile = 6;
-constexpr int kClasses = 4;      // spill classes per tile bucket (see k_sort.cu)
-constexpr int kMaxSupport = 16;  // W <= 16: one warp evaluates both 1D kernel profiles
+constexpr int kMaxSupport = 16;  // W <= 16
+constexpr int kColBlocks = 16;   // sub-buckets per row (by tap-start column), to spread the
+                                 // histogram atomics; a row's sub-buckets are contiguous
 constexpr uint32_t kDropKey = 0xFFFFFFFFu;
-constexpr int kFracBits = 24;    // sub-cell offset quantisation: 2^-24 cell
 
 // counters[] slots in the workspace
-enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_SLOTS = 8 };
+enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_WORK = 4, CNT_SLOTS = 8 };
 
-// 16-byte sorted record: tap start within its tile (8 bits) and the sub-cell
-// offset g = i0 - (x - W/2) in [0,1) quantised to 24 bits, per axis; weighted value.
+// 16-byte sorted record of a visibility filed under (image, plane, row j0): tap start
+// i0 (14 bits, N <= 16384) and the sub-cell offsets g_x, g_y in [0,1) quantised to 24
+// bits, packed as  xpack = i0 << 18 | g_x >> 6,  ypack = (g_x & 63) << 24 | g_y;  then
+// the weighted value.
 struct __align__(16) Record {
   uint32_t xpack;
   uint32_t ypack;
   float vre;
   float vim;
 };
+
+__host__ __device__ __forceinline__ int rec_i0(const Record &r) { return (int)(r.xpack >> 18); }
+__device__ __forceinline__ float rec_gx(const Record &r) {
+  return (float)(((r.xpack & 0x3FFFFu) << 6) | (r.ypack >> 24)) * (1.0f / 16777216.0f);
+}
+__device__ __forceinline__ float rec_gy(const Record &r) {
+  return (float)(r.ypack & 0xFFFFFFu) * (1.0f / 16777216.0f);
+}
 
 struct KernelParams {
   int kind;        // WST_KERNEL_*
@@ -51,6 +59,7 @@ struct Workspace {
   uint32_t *scan_tmp;  // scan partial sums
   unsigned long long *counters;  // CNT_* slots
   uint32_t *wminmax;   // per image: ordered-int min and max of finite w
+  uint8_t *occ;        // per (plane of the chunk, row): 1 if any visibility reaches the row
   float2 *planes;      // chunk of planes
   float2 *comp;        // Kahan compensation image [batch][N*N]
   size_t bytes;
@@ -63,7 +72,7 @@ struct wst_plan_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   // geometry
-  int n = 0, log2n = 0, W = 0, tiles = 0, n_w = 0, batch = 1, n_planes = 0, chunk = 0;
+  int n = 0, log2n = 0, W = 0, n_w = 0, batch = 1, n_planes = 0, chunk = 0;
   int fa = 0, fb = 0;  // four-step column split N = fa * fb (fa contiguous block rows)
   int64_t n_buckets = 0;
   // owned device tables
@@ -224,15 +233,16 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
 cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, int64_t n_bound);
 int64_t scan_tmp_words(int64_t n);
 
-// k_grid.cu
-cudaError_t grid_planes(wst_plan_s *p, int p0, int p1, float2 *out, bool checker);
-cudaError_t degrid_planes(wst_plan_s *p, int p0, int p1, const float2 *planes, float2 *dvis);
-cudaError_t kernel_grad_planes(wst_plan_s *p, int p0, int p1, const float2 *planes, float *dtab);
+// k_rowgrid.cu
+cudaError_t grid_rows(wst_plan_s *p, int p0, int p1, float2 *out, bool fft);
+cudaError_t rows_adjoint(wst_plan_s *p, int p0, int p1, const float2 *planes, float2 *dvis, float *dtab);
 
 // k_fft.cu
 cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool presign,
                      bool postsign);
-cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first);
+// occ (nullable): per (plane of the call, row) 0 if the row is known to be zero
+cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first,
+                       const uint8_t *occ);
 // forward: accumulate planes [p0,p1) (stored at planes[0..]) into image (+comp)
 cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1,
                                   float2 *image, float2 *comp, bool kahan, bool correct,
