@@ -29,32 +29,71 @@ __device__ __forceinline__ void zero_row(float2 *srow, int jt) {
   for (int i = jt; i < N / 2; i += RowCfg<N>::TPR) p[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
+// The W x-taps G(a - W/2 + g_x), a = 0 .. W-1.  For the Gaussian, three exponentials
+// instead of W: with t = g_x - W/2, G(t + a + 1) / G(t + a) = R q^a, R = exp(-(2t + 1) c),
+// q = exp(-2c), c = 1/(2 sigma^2).
+template <int WT>
+__device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q, float (&g)[WT]) {
+  if (kp.kind == WST_KERNEL_GAUSS) {
+    const float t = gx - kp.half;
+    float ga = expf(-t * t * kp.inv2s2);
+    float ra = expf(-(2.0f * t + 1.0f) * kp.inv2s2);
+#pragma unroll
+    for (int a = 0; a < WT; ++a) {
+      g[a] = ga;
+      ga *= ra;
+      ra *= q;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < WT; ++a) g[a] = kernel_eval(kp, (float)a - kp.half + gx);
+  }
+}
+
 // Accumulate the visibilities of rows j0 = q - d_lo ... q into the row, stored planar
 // (re[0..N), im[0..N)).  Their sub-buckets are contiguous in the sorted records, so the
 // range bnd[0] .. bnd[d_lo + 1] is split evenly over the row's threads, one visibility
-// per thread; bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0 fixes the support at
-// compile time.
+// per thread (two in flight); bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0
+// fixes the support at compile time.
 template <int N, int WT>
 __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *__restrict__ rec,
                                          const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt) {
   constexpr int TPR = RowCfg<N>::TPR;
-  const int W = WT > 0 ? WT : kp.support;
   const uint32_t s_end = bnd[d_lo + 1];
-  for (uint32_t s = bnd[0] + jt; s < s_end; s += TPR) {
-    int i = d_lo;
-    while (s < bnd[i]) --i;  // the last row starting at or before s
-    const Record r = rec[s];
-    const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
-    const float gx = rec_gx(r);
-    const int i0 = rec_i0(r);
-    if constexpr (WT > 0) {
+  if constexpr (WT > 0) {
+    const float q = expf(-2.0f * kp.inv2s2);
+    for (uint32_t s = bnd[0] + jt; s < s_end; s += 2 * TPR) {
+      const uint32_t sp[2] = {s, s + TPR};
+      const bool two = sp[1] < s_end;
+      Record r[2];
+      r[0] = rec[sp[0]];
+      if (two) r[1] = rec[sp[1]];
 #pragma unroll
-      for (int a = 0; a < WT; ++a) {
-        const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
-        atomicAdd(&sre[i0 + a], r.vre * g);
-        atomicAdd(&sim[i0 + a], r.vim * g);
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        int i = d_lo;
+        while (sp[h] < bnd[i]) --i;  // the last row starting at or before the record
+        const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r[h]));
+        float g[WT];
+        x_taps<WT>(kp, rec_gx(r[h]), q, g);
+        const int i0 = rec_i0(r[h]);
+        const float vre = r[h].vre * gy, vim = r[h].vim * gy;
+#pragma unroll
+        for (int a = 0; a < WT; ++a) {
+          atomicAdd(&sre[i0 + a], vre * g[a]);
+          atomicAdd(&sim[i0 + a], vim * g[a]);
+        }
       }
-    } else {
+    }
+  } else {
+    const int W = kp.support;
+    for (uint32_t s = bnd[0] + jt; s < s_end; s += TPR) {
+      int i = d_lo;
+      while (s < bnd[i]) --i;
+      const Record r = rec[s];
+      const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
+      const float gx = rec_gx(r);
+      const int i0 = rec_i0(r);
       for (int a = 0; a < W; ++a) {
         const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
         atomicAdd(&sre[i0 + a], r.vre * g);

@@ -220,25 +220,47 @@ static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cuda
   return cudaGetLastError();
 }
 
-// pass 2: scatter records to their sorted position
+// pass 2: scatter records to their sorted position (kScatterIlp visibilities in flight
+// per thread: the loads of the key, its bucket offset and the value are independent
+// across them)
+constexpr int kScatterIlp = 4;
+
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
                           const uint4 *__restrict__ keyinfo, const uint32_t *__restrict__ offsets,
-                          int64_t n_vis, Record *records, uint32_t *perm, float *rweight) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_vis;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 ki = keyinfo[j];
-    if (ki.x == kDropKey) continue;
-    const uint32_t pos = offsets[ki.x] + ki.y;
-    const float2 val = vis[j];
-    const float wt = weight ? weight[j] : 1.0f;
-    Record r;
-    r.xpack = ki.z;
-    r.ypack = ki.w;
-    r.vre = val.x * wt;
-    r.vim = val.y * wt;
-    records[pos] = r;
-    perm[pos] = (uint32_t)j;
-    if (rweight) rweight[pos] = wt;
+                          int64_t n_vis, Record *__restrict__ records, uint32_t *__restrict__ perm,
+                          float *__restrict__ rweight) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n_vis; j0 += stride * kScatterIlp) {
+    uint4 ki[kScatterIlp];
+#pragma unroll
+    for (int h = 0; h < kScatterIlp; ++h) {
+      const int64_t j = j0 + h * stride;
+      ki[h] = j < n_vis ? keyinfo[j] : make_uint4(kDropKey, 0u, 0u, 0u);
+    }
+    uint32_t pos[kScatterIlp];
+    float2 val[kScatterIlp];
+    float wt[kScatterIlp];
+#pragma unroll
+    for (int h = 0; h < kScatterIlp; ++h) {
+      const int64_t j = j0 + h * stride;
+      if (ki[h].x != kDropKey) {
+        pos[h] = offsets[ki[h].x] + ki[h].y;
+        val[h] = vis[j];
+        wt[h] = weight ? weight[j] : 1.0f;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kScatterIlp; ++h) {
+      if (ki[h].x == kDropKey) continue;
+      Record r;
+      r.xpack = ki[h].z;
+      r.ypack = ki[h].w;
+      r.vre = val[h].x * wt[h];
+      r.vim = val[h].y * wt[h];
+      records[pos[h]] = r;
+      perm[pos[h]] = (uint32_t)(j0 + h * stride);
+      if (rweight) rweight[pos[h]] = wt[h];
+    }
   }
 }
 

@@ -12,8 +12,9 @@
 namespace wst {
 
 constexpr int kMaxSupport = 16;  // W <= 16
-constexpr int kColBlocks = 16;   // sub-buckets per row (by tap-start column), to spread the
-                                 // histogram atomics; a row's sub-buckets are contiguous
+constexpr int kColBlocks = 1;    // sub-buckets per row (by tap-start column; a row's sub-buckets
+                                 // are contiguous).  More than one spreads the histogram atomics
+                                 // but enlarges the offsets table and the scan: slower at 16384^2.
 constexpr uint32_t kDropKey = 0xFFFFFFFFu;
 
 // counters[] slots in the workspace
