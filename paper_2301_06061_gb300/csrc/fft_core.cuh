@@ -189,6 +189,58 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const Tw
   }
 }
 
+// Twiddles of stage S held in registers, for kernels that run the same transform many
+// times (one per w-plane): twp[b (R - 1) + r - 1] is the factor of input r of butterfly b.
+template <int L, int EPT, int S>
+constexpr int stage_tw_count() {
+  return stage_ns(L, EPT, S) > 1 ? (EPT / stage_radix(L, EPT, S)) * (stage_radix(L, EPT, S) - 1) : 0;
+}
+template <int L, int EPT, int S>
+constexpr int stage_tw_offset() {  // position of stage S's factors in the concatenated list
+  if constexpr (S == 0) return 0;
+  else return stage_tw_offset<L, EPT, S - 1>() + stage_tw_count<L, EPT, S - 1>();
+}
+template <int L, int EPT>
+constexpr int total_tw_count() {
+  return stage_tw_offset<L, EPT, num_stages(L, EPT)>();
+}
+
+template <int L, int EPT, int TPL, int S, int DIR>
+__device__ __forceinline__ void stage_twiddles(float2 *twp, int jt, const Tw &tw, int twscale) {
+  constexpr int R = stage_radix(L, EPT, S);
+  constexpr int NS = stage_ns(L, EPT, S);
+  if constexpr (NS > 1) {
+#pragma unroll
+    for (int b = 0; b < EPT / R; ++b) {
+      const int k = (jt + b * TPL) % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) twp[b * (R - 1) + r - 1] = twiddle(tw, k * r * (L / (NS * R)) * twscale, DIR);
+    }
+  }
+}
+
+template <int L, int EPT, int TPL, int DIR, int S = 0>
+__device__ __forceinline__ void all_twiddles(float2 *twp, int jt, const Tw &tw, int twscale) {
+  if constexpr (S < num_stages(L, EPT)) {
+    stage_twiddles<L, EPT, TPL, S, DIR>(twp + stage_tw_offset<L, EPT, S>(), jt, tw, twscale);
+    all_twiddles<L, EPT, TPL, DIR, S + 1>(twp, jt, tw, twscale);
+  }
+}
+
+template <int L, int EPT, int S, int DIR>
+__device__ __forceinline__ void stage_compute_pre(float2 (&v)[EPT], const float2 *twp) {
+  constexpr int R = stage_radix(L, EPT, S);
+  constexpr int NS = stage_ns(L, EPT, S);
+#pragma unroll
+  for (int b = 0; b < EPT / R; ++b) {
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], twp[stage_tw_offset<L, EPT, S>() + b * (R - 1) + r - 1]);
+    }
+    dft<R, DIR>(&v[b * R]);
+  }
+}
+
 template <int L, int EPT, int TPL, int S>
 __device__ __forceinline__ int in_index(int jt, int b, int r) {
   constexpr int R = stage_radix(L, EPT, S);
@@ -226,6 +278,30 @@ __device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *
       __syncthreads();  // every load of this stage done before the next stores
       stage_compute<L, EPT, TPL, S, DIR>(v, jt, tw, twscale);
       middle_stages<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, tw, twscale);
+    }
+  }
+}
+
+// middle_stages with the twiddles from registers (the full list of all_twiddles)
+template <int L, int EPT, int TPL, int S, int DIR, class SMI>
+__device__ __forceinline__ void middle_stages_pre(float2 (&v)[EPT], int jt, float2 *sm, SMI smi, const float2 *twp) {
+  constexpr int NST = num_stages(L, EPT);
+  if constexpr (S < NST) {
+    constexpr int RP = stage_radix(L, EPT, S - 1);
+#pragma unroll
+    for (int b = 0; b < EPT / RP; ++b)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) sm[smi(out_index<L, EPT, TPL, S - 1>(jt, b, r))] = v[b * RP + r];
+    __syncthreads();
+    constexpr int R = stage_radix(L, EPT, S);
+#pragma unroll
+    for (int b = 0; b < EPT / R; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = sm[smi(in_index<L, EPT, TPL, S>(jt, b, r))];
+    if constexpr (S + 1 < NST) {
+      __syncthreads();
+      stage_compute_pre<L, EPT, S, DIR>(v, twp);
+      middle_stages_pre<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, twp);
     }
   }
 }

@@ -264,24 +264,28 @@ struct ScreenCtx {
   const float *corr;       // 1/Ghat
 };
 
-// exact screen of plane P and per-plane step at pixel (kp, kq), both times `scale`
-template <bool FP64S>
+// exact screen of plane P at pixel (kp, kq) times `scale`, and (STEP) the per-plane step
+template <bool FP64S, bool STEP = true>
 __device__ __forceinline__ void screen_anchor(const ScreenCtx &sc, int kp, int kq, int P, int img, float scale,
                                               float2 &scr, float2 &stp) {
-  scr = stp = make_float2(0.0f, 0.0f);
+  scr = make_float2(0.0f, 0.0f);
+  if (STEP) stp = make_float2(0.0f, 0.0f);
   if constexpr (FP64S) {
     const double r2 = sc.l2d[kp] + sc.l2d[kq];
     if (!(r2 < 1.0)) return;
     const double t = -r2 / (1.0 + sqrt(1.0 - r2));
     scr = cis_cycles_d(sc.wcd[P] * t);
-    stp = cis_cycles_d(sc.wrange[4 * img + 2] * t);
+    if (STEP) stp = cis_cycles_d(sc.wrange[4 * img + 2] * t);
   } else {
     bool valid;
     const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
     if (!valid) return;
-    const float2 w = sc.wc[P], dw = sc.dwff[img];
+    const float2 w = sc.wc[P];
     scr = cis_cycles_ff(ff_mul({w.x, w.y}, t));
-    stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
+    if (STEP) {
+      const float2 dw = sc.dwff[img];
+      stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
+    }
   }
   scr.x *= scale;
   scr.y *= scale;
@@ -337,6 +341,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   constexpr int R0 = stage_radix(LA, EPT, 0);
   __shared__ float2 sm[LA * C::PADW];
   __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
+  __shared__ float2 s_step[EPT][C::THREADS];  // per-plane screen step of each output (thread-private)
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
@@ -345,6 +350,9 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   auto smi = [col](int i) { return i * C::PADW + col; };
   const bool kahan = flags & ACC_KAHAN;
   const size_t plane_elems = (size_t)n * n;
+  // the same length-LA transform runs once per plane: its twiddles stay in registers
+  float2 twr[total_tw_count<LA, EPT>() > 0 ? total_tw_count<LA, EPT>() : 1];
+  all_twiddles<LA, EPT, TPL, 1>(twr, jt, tw, B);
   stage_tile_async<LA>(stage_buf[0], planes, n, LA * c, col0);
   cp_async_commit();
   int P = p0;
@@ -352,7 +360,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
     const int img = P / n_w;
     const int pstart = P;
     const int pend = min(p1, (img + 1) * n_w);
-    float2 s[EPT], cc[EPT], scr[EPT], stp[EPT];
+    float2 s[EPT], cc[EPT], scr[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) s[e] = cc[e] = make_float2(0.0f, 0.0f);
     for (; P < pend; ++P) {
@@ -363,13 +371,16 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       cp_async_wait<1>();
       __syncthreads();
       if ((P - pstart) % kAnchor == 0) {
+        // the step e^{2 pi i dw t} is one number per pixel and image: evaluated once
 #pragma unroll
         for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
           for (int r = 0; r < RL; ++r) {
             const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-            screen_anchor<FP64S>(sc, kp, kq, P, img, ((kq + kp) & 1) ? -1.0f : 1.0f, scr[b * RL + r],
-                                 stp[b * RL + r]);
+            const float sg = ((kq + kp) & 1) ? -1.0f : 1.0f;
+            float2 &st = s_step[b * RL + r][threadIdx.x];
+            if (P == pstart) screen_anchor<FP64S, true>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
+            else screen_anchor<FP64S, false>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
           }
       }
       const float2 *tile = stage_buf[(P - p0) & 1];
@@ -378,17 +389,17 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
         for (int r = 0; r < R0; ++r) v[b * R0 + r] = tile[in_index<LA, EPT, TPL, 0>(jt, b, r) * kCB + col];
-      stage_compute<LA, EPT, TPL, 0, 1>(v, jt, tw, B);
+      stage_compute_pre<LA, EPT, 0, 1>(v, twr);
       if constexpr (NST > 1) {
-        middle_stages<LA, EPT, TPL, 1, 1>(v, jt, sm, smi, tw, B);
-        stage_compute<LA, EPT, TPL, NST - 1, 1>(v, jt, tw, B);
+        middle_stages_pre<LA, EPT, TPL, 1, 1>(v, jt, sm, smi, twr);
+        stage_compute_pre<LA, EPT, NST - 1, 1>(v, twr);
       }
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
         const float2 y = cmul(v[e], scr[e]);
         if (kahan) kahan_add(s[e], cc[e], y);
         else s[e] = cadd(s[e], y);
-        scr[e] = cmul(scr[e], stp[e]);
+        scr[e] = cmul(scr[e], s_step[e][threadIdx.x]);
       }
       __syncthreads();  // staging buffer and shared memory reused by the next planes
     }

@@ -137,8 +137,12 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
     if (valid && jt == 0) occ[(int64_t)pl * N + q] = empty ? 0 : 1;
     if constexpr (RPC == 1) {
       if (empty) {  // uniform across the CTA: one row per step
-        float4 *o4 = reinterpret_cast<float4 *>(orow);
-        for (int i = jt; i < N / 2; i += TPR) o4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // the column pass reads only occupied rows (occ), so transformed empty rows are
+        // not written; plain gridding hands the planes to the caller and writes zeros
+        if constexpr (!FFT) {
+          float4 *o4 = reinterpret_cast<float4 *>(orow);
+          for (int i = jt; i < N / 2; i += TPR) o4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
         continue;
       }
     }
@@ -164,7 +168,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       stage_compute<N, EPT, TPR, 0, 1>(v, jt, tw, 1);
       middle_stages<N, EPT, TPR, 1, 1>(v, jt, srow, smi, tw, 1);
       stage_compute<N, EPT, TPR, NST - 1, 1>(v, jt, tw, 1);
-      if (valid) {
+      if (valid && !empty) {
 #pragma unroll
         for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
