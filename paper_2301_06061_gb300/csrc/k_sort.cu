@@ -53,20 +53,81 @@ __global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax)
 struct SortGeom {
   int n, W, n_w;
   double half_n, half_w, fov;
+  float fov_hi, fov_lo;    // fov as a float-float pair
+  float half_nf, half_wf;  // N/2 and W/2 (exact in FP32)
 };
+
+// The placement decisions (tap start ceil(x - W/2), plane floor((w - w_lo) scale)) are
+// those of the FP64 expressions below.  They are taken from float-float values (about
+// 46 significant bits, no FP64 instruction) whenever the float-float value is farther
+// from the decision boundary than its error bound allows, and from the FP64 expressions
+// otherwise (a few visibilities in 10^7).
+
+// FP64 reference placement of one visibility (the rare path)
+__device__ __noinline__ void place_fp64(float uf, float vf, float wf, const SortGeom &g, double w_lo, double scale,
+                                        int &ci_out, int &cj_out, int &k_out, bool &dropped, uint32_t &fx,
+                                        uint32_t &fy) {
+  const double x = __dadd_rn(g.half_n, __dmul_rn((double)uf, g.fov));
+  const double y = __dadd_rn(g.half_n, __dmul_rn((double)vf, g.fov));
+  const double hx = __dsub_rn(x, g.half_w), hy = __dsub_rn(y, g.half_w);
+  const double ci = ceil(hx), cj = ceil(hy);
+  dropped = ci < 0.0 || cj < 0.0 || ci + g.W > g.n || cj + g.W > g.n;
+  ci_out = cj_out = k_out = 0;
+  fx = fy = 0u;
+  if (dropped) return;
+  if (scale > 0.0) {
+    const double q = floor(__dmul_rn(__dsub_rn((double)wf, w_lo), scale));
+    k_out = q < 0.0 ? 0 : (q > g.n_w - 1 ? g.n_w - 1 : (int)q);
+  }
+  ci_out = (int)ci;
+  cj_out = (int)cj;
+  // exact offsets in [0, 1), quantised to 2^-24 (round to nearest, kept below 1)
+  const double gx = __dsub_rn(ci, hx), gy = __dsub_rn(cj, hy);
+  fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
+  fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// hx = half_n + u fov - half_w as hi + lo (|error| below 2^-46 (|u fov| + n))
+__device__ __forceinline__ void tap_arg_ff(float uf, const SortGeom &g, float &hi, float &lo) {
+  const float ph = __fmul_rn(uf, g.fov_hi);
+  const float pe = __fmaf_rn(uf, g.fov_hi, -ph);  // u fov_hi - ph, exactly
+  const float pl = __fmaf_rn(uf, g.fov_lo, pe);
+  float sh, se, th, te;
+  two_sum_f(g.half_nf, ph, sh, se);
+  two_sum_f(sh, -g.half_wf, th, te);
+  hi = th;
+  lo = __fadd_rn(__fadd_rn(se, te), pl);
+}
+
+// c + floor/ceil decision of hi + lo against the integers around floor(hi):
+// returns e0 = (hi + lo) - floor(hi) and e1 = floor(hi) + 1 - (hi + lo); the
+// one near zero is accurate because its leading part is exact
+__device__ __forceinline__ void frac_ff(float hi, float lo, float &fl, float &e0, float &e1) {
+  fl = floorf(hi);
+  const float fr = __fsub_rn(hi, fl);  // exact
+  e0 = __fadd_rn(fr, lo);
+  e1 = __fsub_rn(__fsub_rn(1.0f, fr), lo);
+}
 
 // pass 1: placement, bucket key, histogram rank (warp-aggregated atomics)
 __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
                        const float *__restrict__ w, const float2 *__restrict__ vis,
                        const float *__restrict__ weight, const int64_t *__restrict__ boff,
-                       const double *__restrict__ wrange, SortGeom g, uint32_t *offsets,
-                       uint4 *keyinfo, unsigned long long *counters) {
+                       const double *__restrict__ wrange, const float4 *__restrict__ wrange_ff, SortGeom g,
+                       uint32_t *offsets, uint4 *keyinfo, unsigned long long *counters) {
   const int img = blockIdx.y;
   const int64_t b0 = boff[img], b1 = boff[img + 1];
-  const double w_lo = wrange[4 * img + 0];
-  const double scale = wrange[4 * img + 1];
+  const float4 wff = wrange_ff[img];  // w_lo (hi, lo), scale (hi, lo)
+  const bool scale_pos = wrange[4 * img + 1] > 0.0;
   const int64_t span = b1 - b0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const float nf = (float)g.n, wn = (float)g.W;
   // uniform trip count across the warp so that the warp-level votes are safe
   const int64_t start = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   for (int64_t base = start; base < span; base += stride) {
@@ -82,25 +143,59 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
       if (!(isfinite(uf) && isfinite(vf) && isfinite(wf) && finite2(val) && isfinite(wt))) {
         nonfinite = true;
       } else {
-        const double x = __dadd_rn(g.half_n, __dmul_rn((double)uf, g.fov));
-        const double y = __dadd_rn(g.half_n, __dmul_rn((double)vf, g.fov));
-        const double hx = __dsub_rn(x, g.half_w), hy = __dsub_rn(y, g.half_w);
-        const double ci = ceil(hx), cj = ceil(hy);
-        if (ci < 0.0 || cj < 0.0 || ci + g.W > g.n || cj + g.W > g.n) {
+        float xh, xl, yh, yl;
+        tap_arg_ff(uf, g, xh, xl);
+        tap_arg_ff(vf, g, yh, yl);
+        float flx, ex0, ex1, fly, ey0, ey1;
+        frac_ff(xh, xl, flx, ex0, ex1);
+        frac_ff(yh, yl, fly, ey0, ey1);
+        // tap start = ceil(hx): fl if hx <= fl, fl + 1 if fl < hx <= fl + 1, else fl + 2
+        const float cxf = flx + (ex0 <= 0.0f ? 0.0f : (ex1 < 0.0f ? 2.0f : 1.0f));
+        const float cyf = fly + (ey0 <= 0.0f ? 0.0f : (ey1 < 0.0f ? 2.0f : 1.0f));
+        const float epsx = (fabsf(xh) + nf) * 0x1p-40f, epsy = (fabsf(yh) + nf) * 0x1p-40f;
+        bool sure = fminf(fabsf(ex0), fabsf(ex1)) > epsx && fminf(fabsf(ey0), fabsf(ey1)) > epsy;
+        // far outside the mesh the decision cannot change: dropped either way
+        const bool out = xh < -4.0f || yh < -4.0f || xh > nf + 4.0f || yh > nf + 4.0f;
+        int ci = 0, cj = 0, k = 0;
+        uint32_t fx = 0, fy = 0;
+        if (out) {
           dropped = true;
+          sure = true;
         } else {
-          int k = 0;
-          if (scale > 0.0) {
-            const double q = floor(__dmul_rn(__dsub_rn((double)wf, w_lo), scale));
-            k = q < 0.0 ? 0 : (q > g.n_w - 1 ? g.n_w - 1 : (int)q);
+          ci = (int)cxf;
+          cj = (int)cyf;
+          dropped = cxf < 0.0f || cyf < 0.0f || cxf + wn > nf || cyf + wn > nf;
+          if (!dropped && scale_pos && !(wff.z > 0.0f)) sure = false;  // scale below FP32 range
+          if (!dropped && scale_pos && wff.z > 0.0f) {
+            // plane = floor((w - w_lo) scale), clamped
+            float dh, de;
+            two_sum_f(wf, -wff.x, dh, de);
+            const float dl = __fsub_rn(de, wff.y);
+            const float qh = __fmul_rn(dh, wff.z);
+            const float ql = __fadd_rn(__fmaf_rn(dh, wff.z, -qh), __fmaf_rn(dh, wff.w, __fmul_rn(dl, wff.z)));
+            if (qh < -2.0f) k = 0;
+            else if (qh > (float)g.n_w + 2.0f) k = g.n_w - 1;
+            else {
+              float flq, eq0, eq1;
+              frac_ff(qh, ql, flq, eq0, eq1);
+              // floor(q): fl if fl <= q < fl + 1, fl - 1 if q < fl, fl + 1 if q >= fl + 1
+              const float kq = flq + (eq0 < 0.0f ? -1.0f : (eq1 <= 0.0f ? 1.0f : 0.0f));
+              const float epsq = (fabsf(wf) * wff.z + fabsf(qh) + 1.0f) * 0x1p-38f;
+              sure = sure && fminf(fabsf(eq0), fabsf(eq1)) > epsq;
+              k = kq < 0.0f ? 0 : (kq > (float)(g.n_w - 1) ? g.n_w - 1 : (int)kq);
+            }
           }
-          const int i0 = (int)ci, j0 = (int)cj;
-          // exact offsets in [0, 1), quantised to 2^-24 (round to nearest, kept below 1)
-          const double gx = __dsub_rn(ci, hx), gy = __dsub_rn(cj, hy);
-          const uint32_t fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
-          const uint32_t fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
-          key = (uint32_t)((((int64_t)img * g.n_w + k) * g.n + j0) * kColBlocks + (int64_t)i0 * kColBlocks / g.n);
-          xpack = ((uint32_t)i0 << 18) | (fx >> 6);
+          if (!dropped) {
+            // offsets g = c - hx in [0, 1): the difference c - hi is exact
+            const float gx = __fsub_rn(__fsub_rn(cxf, xh), xl), gy = __fsub_rn(__fsub_rn(cyf, yh), yl);
+            fx = min(__float2uint_rn(fmaxf(gx, 0.0f) * 16777216.0f), 16777215u);
+            fy = min(__float2uint_rn(fmaxf(gy, 0.0f) * 16777216.0f), 16777215u);
+          }
+        }
+        if (!sure) place_fp64(uf, vf, wf, g, wrange[4 * img + 0], wrange[4 * img + 1], ci, cj, k, dropped, fx, fy);
+        if (!dropped) {
+          key = (uint32_t)((((int64_t)img * g.n_w + k) * g.n + cj) * kColBlocks + (int64_t)ci * kColBlocks / g.n);
+          xpack = ((uint32_t)ci << 18) | (fx >> 6);
           ypack = ((fx & 63u) << 24) | fy;
           kept = true;
         }
@@ -298,7 +393,11 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   g.half_n = 0.5 * p->n;
   g.half_w = 0.5 * p->W;
   g.fov = p->cfg.fov;
-  k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, g, ws.offsets,
+  g.fov_hi = (float)g.fov;
+  g.fov_lo = (float)(g.fov - (double)g.fov_hi);
+  g.half_nf = (float)g.half_n;
+  g.half_wf = (float)g.half_w;
+  k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, p->wrange_ff, g, ws.offsets,
                                ws.keyinfo, ws.counters);
   p->launches += 1;
   if ((e = cudaGetLastError())) return e;

@@ -108,7 +108,7 @@ __device__ __forceinline__ float ordered_to_float(uint32_t o) {
   return __uint_as_float(b);
 }
 
-__global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre_d, float2 *dwff,
+__global__ void k_plane_centres(double *wrange, float4 *wrange_ff, float2 *wcentre, double *wcentre_d, float2 *dwff,
                                 const uint32_t *wminmax, int batch, int n_w, double cfg_lo,
                                 double cfg_hi, int from_data) {
   int img = blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,6 +130,8 @@ __global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre
   wrange[4 * img + 2] = dw;
   wrange[4 * img + 3] = hi;
   dwff[img] = ff_split(dw);
+  const float2 lo_ff = ff_split(lo), sc_ff = ff_split(scale);
+  wrange_ff[img] = make_float4(lo_ff.x, lo_ff.y, sc_ff.x, sc_ff.y);
   for (int k = 0; k < n_w; ++k) {
     double wk = lo + ((double)k + 0.5) * dw;
     wcentre[img * n_w + k] = ff_split(wk);
@@ -140,7 +142,7 @@ __global__ void k_plane_centres(double *wrange, float2 *wcentre, double *wcentre
 cudaError_t build_plane_centres(wst_plan_s *p) {
   const bool from_data = p->cfg.w_min == p->cfg.w_max;
   k_plane_centres<<<(p->batch + 63) / 64, 64, 0, p->stream>>>(
-      p->wrange, p->wcentre, p->wcentre_d, p->dwff, p->W_.wminmax, p->batch, p->n_w, p->cfg.w_min,
+      p->wrange, p->wrange_ff, p->wcentre, p->wcentre_d, p->dwff, p->W_.wminmax, p->batch, p->n_w, p->cfg.w_min,
       p->cfg.w_max, from_data ? 1 : 0);
   p->launches += 1;
   return cudaGetLastError();

@@ -91,6 +91,7 @@ void destroy_tables(wst_plan_s *p) {
   cudaFree(p->l2d);
   cudaFree(p->ktable);
   cudaFree(p->wrange);
+  cudaFree(p->wrange_ff);
   cudaFree(p->wcentre);
   cudaFree(p->wcentre_d);
   cudaFree(p->dwff);
@@ -190,6 +191,7 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   ALLOC(p->l2ff, c.n);
   ALLOC(p->l2d, c.n);
   ALLOC(p->wrange, 4 * c.batch);
+  ALLOC(p->wrange_ff, c.batch);
   ALLOC(p->wcentre, p->n_planes);
   ALLOC(p->wcentre_d, p->n_planes);
   ALLOC(p->dwff, c.batch);

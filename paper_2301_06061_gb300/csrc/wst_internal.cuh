@@ -83,6 +83,7 @@ struct wst_plan_s {
   double *l2d = nullptr;     // l_a^2 in FP64 (WST_FLAG_FP64_SCREEN)
   float *ktable = nullptr;   // TABLE kernel samples
   double *wrange = nullptr;  // per image: w_lo, scale = n_w/(w_hi-w_lo), dw, w_hi
+  float4 *wrange_ff = nullptr;  // per image: w_lo and scale as float-float pairs
   float2 *wcentre = nullptr; // per global plane: centre w_k as float-float
   double *wcentre_d = nullptr;  // per global plane: centre w_k (FP64)
   float2 *dwff = nullptr;    // per image: plane spacing dw as float-float

@@ -107,6 +107,47 @@ def test_vis_cells_bit_exact(wst):
     assert s["n_nonfinite"] == int((st == 2).sum()) == 8
 
 
+def near_integer_coords(n, fov, W, rng, count=600):
+    """u with half_n + u fov - W/2 on, or a few FP32 steps from, an integer tap start,
+    including the tap starts where the drop rule switches (0 and n - W)."""
+    m = np.concatenate([rng.integers(-3, n + 3, count - 8), [0, -1, 1, n - W, n - W + 1, n - W - 1, n // 2, 3]])
+    u = ((m - n / 2 + W / 2) / fov).astype(np.float32)
+    steps = rng.integers(-2, 3, m.size).astype(np.int32)
+    out = u.copy()
+    for k in range(1, 3):  # move by `steps` FP32 ulps
+        out = np.where(steps >= k, np.nextafter(out, np.float32(np.inf)), out)
+        out = np.where(steps <= -k, np.nextafter(out, np.float32(-np.inf)), out)
+    return out
+
+
+@pytest.mark.parametrize("n,fov,W", [(256, 0.1, 7), (16384, 0.5, 7), (4096, 0.2, 8)])
+def test_vis_cells_near_decision_boundaries(wst, n, fov, W):
+    """Tap starts and planes decided on or next to their boundaries agree bit for bit with
+    the FP64 oracle (the float-float fast path must defer to FP64 there)."""
+    rng = np.random.default_rng(n + W)
+    u = near_integer_coords(n, fov, W, rng)
+    v = rng.permutation(near_integer_coords(n, fov, W, rng))
+    n_w, lo, hi = 8, -200.0, 200.0
+    edges = lo + np.arange(n_w + 1) * (hi - lo) / n_w
+    w = np.repeat(edges, -(-u.size // edges.size))[: u.size].astype(np.float32)
+    steps = rng.integers(-2, 3, u.size)
+    w = np.where(steps > 0, np.nextafter(w, np.float32(np.inf)), np.where(steps < 0, np.nextafter(w, np.float32(-np.inf)), w))
+    w = rng.permutation(w.astype(np.float32))
+    vis = np.ones(u.size, np.complex64)
+    cfg = wst.Config(n=n, fov=fov, n_w=n_w, w_min=lo, w_max=hi, support=W, kparam=wst.DEFAULT_SIGMA[W],
+                     planes_per_chunk=1)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    k = torch.empty(u.size, dtype=torch.int32, device="cuda")
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    ko, io, jo, st = oracle.locate(ocfg_for(cfg, lo, hi), u, v, w, vis)
+    np.testing.assert_array_equal(i0.cpu().numpy(), io)
+    np.testing.assert_array_equal(j0.cpu().numpy(), jo)
+    np.testing.assert_array_equal(k.cpu().numpy(), ko)
+    s = plan.stats()
+    assert s["n_kept"] == int((st == 0).sum()) and s["n_dropped"] == int((st == 1).sum()) > 0
+
+
 def test_w_range_from_data(wst):
     u, v, w, vis = make_case(n=128, n_vis=5000)
     cfg = wst.Config(n=128, fov=0.1, n_w=5)  # w_min == w_max: from the data
