@@ -65,9 +65,9 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
     for (uint32_t s = bnd[0] + jt; s < s_end; s += 2 * TPR) {
       const uint32_t sp[2] = {s, s + TPR};
       const bool two = sp[1] < s_end;
-      Record r[2];
-      r[0] = rec[sp[0]];
-      if (two) r[1] = rec[sp[1]];
+      RecHead r[2];
+      r[0] = rec_head(rec, sp[0]);
+      if (two) r[1] = rec_head(rec, sp[1]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (h == 1 && !two) break;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
     for (uint32_t s = bnd[0] + jt; s < s_end; s += TPR) {
       int i = d_lo;
       while (s < bnd[i]) --i;
-      const Record r = rec[s];
+      const RecHead r = rec_head(rec, s);
       const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
       const float gx = rec_gx(r);
       const int i0 = rec_i0(r);
@@ -188,8 +188,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
 template <int N, bool KGRAD>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
 k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec,
-               const uint32_t *__restrict__ off, const uint32_t *__restrict__ perm,
-               const float *__restrict__ rweight, int p0, int np, KernelParams kp,
+               const uint32_t *__restrict__ off, int p0, int np, KernelParams kp,
                float2 *__restrict__ dvis, float *__restrict__ dtab,
                unsigned long long *__restrict__ counter, Tw tw) {
   using C = RowCfg<N>;
@@ -248,7 +247,7 @@ k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec
         const uint32_t s0 = off[(b0 + q - d) * kColBlocks], s1 = off[(b0 + q - d + 1) * kColBlocks];
         const float ty = (float)d - kp.half;
         for (uint32_t s = s0 + jt; s < s1; s += TPR) {
-          const Record rc = rec[s];
+          const RecHead rc = rec_head(rec, s);
           const float targ_y = ty + rec_gy(rc);
           const float gy = kernel_eval(kp, targ_y);
           const float gx0 = rec_gx(rc);
@@ -260,8 +259,9 @@ k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec
               are = fmaf(g, cell[a].x, are);
               aim = fmaf(g, cell[a].y, aim);
             }
-            const float wt = (rweight ? rweight[s] : 1.0f) * gy;
-            const uint32_t j = perm[s];
+            const uint2 tail = __ldg(reinterpret_cast<const uint2 *>(rec + s) + 2);  // index, weight
+            const float wt = __uint_as_float(tail.y) * gy;
+            const uint32_t j = tail.x;
             atomicAdd(&dvis[j].x, wt * are);
             atomicAdd(&dvis[j].y, wt * aim);
           } else {
@@ -358,8 +358,7 @@ static cudaError_t launch_rows_adjoint(wst_plan_s *p, int p0, int np, const floa
   unsigned long long *counter = p->W_.counters + CNT_WORK;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
-  kern<<<grid, C::THREADS, smem, p->stream>>>(planes, p->W_.records, p->W_.offsets, p->W_.perm,
-                                             p->has_weight ? p->W_.rweight : nullptr, p0, np, kernel_params(p),
+  kern<<<grid, C::THREADS, smem, p->stream>>>(planes, p->W_.records, p->W_.offsets, p0, np, kernel_params(p),
                                              dvis, dtab, counter, tw_half(p));
   return cudaGetLastError();
 }

@@ -322,8 +322,7 @@ constexpr int kScatterIlp = 4;
 
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
                           const uint4 *__restrict__ keyinfo, const uint32_t *__restrict__ offsets,
-                          int64_t n_vis, Record *__restrict__ records, uint32_t *__restrict__ perm,
-                          float *__restrict__ rweight) {
+                          int64_t n_vis, Record *__restrict__ records) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n_vis; j0 += stride * kScatterIlp) {
     uint4 ki[kScatterIlp];
@@ -347,14 +346,9 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
 #pragma unroll
     for (int h = 0; h < kScatterIlp; ++h) {
       if (ki[h].x == kDropKey) continue;
-      Record r;
-      r.xpack = ki[h].z;
-      r.ypack = ki[h].w;
-      r.vre = val[h].x * wt[h];
-      r.vim = val[h].y * wt[h];
-      records[pos[h]] = r;
-      perm[pos[h]] = (uint32_t)(j0 + h * stride);
-      if (rweight) rweight[pos[h]] = wt[h];
+      uint4 *dst = reinterpret_cast<uint4 *>(records + pos[h]);
+      dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(val[h].x * wt[h]), __float_as_uint(val[h].y * wt[h]));
+      dst[1] = make_uint4((uint32_t)(j0 + h * stride), __float_as_uint(wt[h]), 0u, 0u);
     }
   }
 }
@@ -403,8 +397,7 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   if ((e = cudaGetLastError())) return e;
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(
-      vis, weight, ws.keyinfo, ws.offsets, p->n_vis, ws.records, ws.perm,
-      weight ? ws.rweight : nullptr);
+      vis, weight, ws.keyinfo, ws.offsets, p->n_vis, ws.records);
   p->launches += 1;
   return cudaGetLastError();
 }
@@ -412,7 +405,7 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
 // ---------------------------------------------------------------------------------
 // per-visibility placement read back from the sorted records (inspection call)
 // ---------------------------------------------------------------------------------
-__global__ void k_vis_cells(const Record *rec, const uint32_t *perm, const uint32_t *offsets,
+__global__ void k_vis_cells(const Record *rec, const uint32_t *offsets,
                             int64_t n_buckets, int64_t n_bound, int n, int n_w,
                             int32_t *plane, int32_t *i0, int32_t *j0) {
   const int64_t n_kept = offsets[n_buckets];  // records beyond it are not written
@@ -425,11 +418,11 @@ __global__ void k_vis_cells(const Record *rec, const uint32_t *perm, const uint3
       int64_t mid = (lo + hi) >> 1;
       if (offsets[mid] <= (uint32_t)s) lo = mid; else hi = mid;
     }
-    const uint32_t j = perm[s];
+    const uint32_t j = rec[s].index;
     const int64_t row_bucket = lo / kColBlocks;
     plane[j] = (int)((row_bucket / n) % n_w);
     j0[j] = (int)(row_bucket % n);
-    i0[j] = rec_i0(rec[s]);
+    i0[j] = rec_i0(rec[s].h);
   }
 }
 
@@ -441,7 +434,7 @@ cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, i
   if ((e = cudaMemsetAsync(j0, 0xFF, sizeof(int32_t) * p->n_vis, s))) return e;
   if (n_bound > 0)
     k_vis_cells<<<grid_for(n_bound, 256, 152 * 16), 256, 0, s>>>(
-        p->W_.records, p->W_.perm, p->W_.offsets, p->n_buckets, n_bound, p->n, p->n_w, plane,
+        p->W_.records, p->W_.offsets, p->n_buckets, n_bound, p->n, p->n_w, plane,
         i0, j0);
   p->launches += 1;
   return cudaGetLastError();

@@ -43,7 +43,7 @@ int ilog2(int x) {
 }
 
 struct Layout {
-  size_t keyinfo_planes, records, perm, rweight, offsets, scan_tmp, counters, wminmax, occ, comp, total;
+  size_t keyinfo_planes, records, offsets, scan_tmp, counters, wminmax, occ, comp, total;
 };
 
 Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
@@ -55,10 +55,6 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   off += align_up(plane_bytes > keyinfo_bytes ? plane_bytes : keyinfo_bytes);
   L.records = off;
   off += align_up((size_t)n_vis * sizeof(Record));
-  L.perm = off;
-  off += align_up((size_t)n_vis * sizeof(uint32_t));
-  L.rweight = off;
-  off += align_up((size_t)n_vis * sizeof(float));
   L.offsets = off;
   off += align_up((size_t)(p->n_buckets + 1) * sizeof(uint32_t));
   L.scan_tmp = off;
@@ -278,8 +274,6 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.keyinfo = (uint4 *)(p->ws + L.keyinfo_planes);
   W.planes = (float2 *)(p->ws + L.keyinfo_planes);
   W.records = (Record *)(p->ws + L.records);
-  W.perm = (uint32_t *)(p->ws + L.perm);
-  W.rweight = (float *)(p->ws + L.rweight);
   W.offsets = (uint32_t *)(p->ws + L.offsets);
   W.scan_tmp = (uint32_t *)(p->ws + L.scan_tmp);
   W.counters = (unsigned long long *)(p->ws + L.counters);

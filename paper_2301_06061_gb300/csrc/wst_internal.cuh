@@ -20,22 +20,39 @@ constexpr uint32_t kDropKey = 0xFFFFFFFFu;
 // counters[] slots in the workspace
 enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_WORK = 4, CNT_SLOTS = 8 };
 
-// 16-byte sorted record of a visibility filed under (image, plane, row j0): tap start
-// i0 (14 bits, N <= 16384) and the sub-cell offsets g_x, g_y in [0,1) quantised to 24
-// bits, packed as  xpack = i0 << 18 | g_x >> 6,  ypack = (g_x & 63) << 24 | g_y;  then
-// the weighted value.
-struct __align__(16) Record {
+// 32-byte sorted record of a visibility filed under (image, plane, row j0).  The head
+// (16 bytes, all the gridder reads): tap start i0 (14 bits, N <= 16384) and the sub-cell
+// offsets g_x, g_y in [0,1) quantised to 24 bits, packed as  xpack = i0 << 18 | g_x >> 6,
+// ypack = (g_x & 63) << 24 | g_y;  then the weighted value.  The tail: the caller's
+// index and weight (adjoint).  One record fills one 32-byte DRAM sector, so the scatter
+// into sorted order writes whole sectors (no read-modify-write of partial sectors).
+struct __align__(16) RecHead {
   uint32_t xpack;
   uint32_t ypack;
   float vre;
   float vim;
 };
+struct __align__(32) Record {
+  RecHead h;
+  uint32_t index;  // caller's visibility index
+  float weight;    // caller's weight (1 without weights)
+  uint32_t pad[2];
+};
 
-__host__ __device__ __forceinline__ int rec_i0(const Record &r) { return (int)(r.xpack >> 18); }
-__device__ __forceinline__ float rec_gx(const Record &r) {
+__device__ __forceinline__ RecHead rec_head(const Record *rec, uint32_t s) {
+  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(rec + s));
+  RecHead h;
+  h.xpack = q.x;
+  h.ypack = q.y;
+  h.vre = __uint_as_float(q.z);
+  h.vim = __uint_as_float(q.w);
+  return h;
+}
+__host__ __device__ __forceinline__ int rec_i0(const RecHead &r) { return (int)(r.xpack >> 18); }
+__device__ __forceinline__ float rec_gx(const RecHead &r) {
   return (float)(((r.xpack & 0x3FFFFu) << 6) | (r.ypack >> 24)) * (1.0f / 16777216.0f);
 }
-__device__ __forceinline__ float rec_gy(const Record &r) {
+__device__ __forceinline__ float rec_gy(const RecHead &r) {
   return (float)(r.ypack & 0xFFFFFFu) * (1.0f / 16777216.0f);
 }
 
@@ -54,8 +71,6 @@ struct KernelParams {
 struct Workspace {
   uint4 *keyinfo;      // per visibility: key, rank, xpack, ypack (aliases the plane buffer)
   Record *records;     // sorted records
-  uint32_t *perm;      // sorted position -> caller index
-  float *rweight;      // sorted position -> weight (only when weights are given)
   uint32_t *offsets;   // bucket offsets [n_buckets + 1]
   uint32_t *scan_tmp;  // scan partial sums
   unsigned long long *counters;  // CNT_* slots
