@@ -180,11 +180,14 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     rel = np.minimum(2.0, 2.0 * np.pi * dmax * nm1) + ea + eb + ea * eb
     bound = sum_abs * rel + 1e-5 * peak
     central = (np.abs(pa - n // 2) < n // 8) & (np.abs(pb - n // 2) < n // 8)
+    inner = (np.abs(pa - n // 2) < 3 * n // 8) & (np.abs(pb - n // 2) < 3 * n // 8)  # central 3/4
     return {"judge": "wst_dft (GPU direct transform of Eq. 2 with float-float phases)",
             "sky": f"{sky.flux.size} point sources, visibilities by Eq. 1 (wst_predict_points)",
             "pixels": int(pa.size), "source_pixels": int(sa.size),
             "max_err_rel_peak": float(err.max() / peak),
             "central_max_err_rel_peak": float(err[central].max() / peak) if central.any() else None,
+            "inner3q_max_err_rel_peak": float(err[inner].max() / peak) if inner.any() else None,
+            "inner3q_rms_err_rel_peak": float(np.sqrt(np.mean(err[inner] ** 2)) / peak) if inner.any() else None,
             "max_err_over_bound": float((err / bound).max()),
             "bound_rel_peak": {"min": float(bound.min() / peak), "median": float(np.median(bound) / peak),
                                "max": float(bound.max() / peak)},
@@ -308,21 +311,44 @@ def oracle_sample(work, vis, plane: int):
 
 
 def time_oracle_sample(work, vis, repeats: int = 1):
-    """Seconds per full job, extrapolated from one plane of the single-image workloads."""
+    """Seconds per full job, extrapolated from one plane of the single-image workloads;
+    also returns the sample and the oracle's image of it."""
     import oracle
 
     plane = work.n_w // 2
     cfg, u, v, w, vv = oracle_sample(work, vis, plane)
     times = []
+    ref = None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.image(cfg, u, v, w, vv)
+        ref = oracle.image(cfg, u, v, w, vv)
         times.append(time.perf_counter() - t0)
     t_plane = statistics.median(times)
     job_s = t_plane * work.n_w  # the job is n_w such planes (plus their share of visibilities)
     sample = (f"w-plane {plane} of {work.n_w} ({u.size} of {work.n_vis} visibilities, {work.n}^2 FP64 grid, "
               f"FFT, screen, correction); time x {work.n_w} planes")
-    return job_s, sample, oracle.num_threads()
+    return job_s, sample, oracle.num_threads(), (cfg, u, v, w, vv, ref)
+
+
+def oracle_parity(torch, wst, dev, sample):
+    """The CUDA path on the oracle's sample (same plane slab, n_w = 1) against the oracle's
+    FP64 image: max error over the central half (|nu| <= 1/4) and over the whole image,
+    relative to the peak."""
+    cfg, u, v, w, vv, ref = sample
+    c = wst.Config(n=cfg.n, fov=cfg.fov, n_w=1, w_min=cfg.w_min, w_max=cfg.w_max, support=cfg.support,
+                   kparam=cfg.kparam, flags=wst.WST_FLAG_KAHAN)
+    plan = wst.Plan(c, device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    plan.set_vis(t(u), t(v), t(w), t(vv))
+    img = plan.image()[0].cpu().numpy().astype(np.complex128)
+    plan.close()
+    n = cfg.n
+    err = np.abs(img - ref)
+    q = slice(n // 4, 3 * n // 4)
+    peak = np.abs(ref).max()
+    return {"sample": f"w-plane slab of the workload, {u.size} visibilities, {n}^2, full image",
+            "central_half_max_err_rel_peak": float(err[q, q].max() / np.abs(ref[q, q]).max()),
+            "max_err_rel_peak": float(err.max() / peak)}
 
 
 # ------------------------------------------------------------------------------------------
@@ -474,9 +500,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and batch == 1:
-        job_s, sample, cores = time_oracle_sample(work, vis_np)
+        job_s, sample, cores, osample = time_oracle_sample(work, vis_np)
         cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
                "sample": sample}
+        if args.kernel == "gauss" and not args.snap_w:  # same kernel as the oracle's sample
+            cpu["parity_vs_oracle"] = oracle_parity(torch, wst, dev, osample)
 
     clocks = clk.summary()
     if rank == 0:
@@ -490,6 +518,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "ggpas": {"end_to_end": round(n_vis * cfg.support ** 2 / (ms_step * 1e-3) / 1e9, 2),
+                      "grid_kernel": round(n_vis * cfg.support ** 2 / (stages["grid"] / args.steps * 1e-3) / 1e9, 2),
+                      "note": "grid-point additions per second (N_vis W^2 / time); the grid kernel also "
+                              "transforms the rows"},
             "gpu_launches": int(st["n_launches"]) * args.steps, "accuracy": acc,
         }
         print(json.dumps(line), flush=True)
@@ -513,7 +545,7 @@ def run_reference(args, rank: int, world: int):
     times = []
     sample = cores = None
     for i in range(args.warmup + args.steps):
-        job_s, sample, cores = time_oracle_sample(work, vis_np)
+        job_s, sample, cores, _ = time_oracle_sample(work, vis_np)
         if i >= args.warmup:
             times.append(job_s)
     job_s = statistics.mean(times)
