@@ -260,10 +260,10 @@ def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept
     """Algorithmic DRAM bytes of one launch of a stage (averaged over the chunks)."""
     S = 8.0 * n * n
     per_chunk_planes = planes / chunks
-    if stage == "sort":  # read u, v, w, V (20 B) and write the record and index (20 B)
-        return 40.0 * n_vis
-    if stage == "grid":  # write every plane cell once, read the records once
-        return per_chunk_planes * S + 16.0 * n_kept / chunks
+    if stage == "sort":  # read u, v, w, V (20 B) and write the 32-byte record
+        return 52.0 * n_vis
+    if stage == "grid":  # write every plane cell once, read the 32-byte records once
+        return per_chunk_planes * S + 32.0 * n_kept / chunks
     if stage in ("rows", "cols_a"):  # read + write each plane
         return 2.0 * per_chunk_planes * S
     if stage == "cols_b":  # read each plane, write the images once
