@@ -103,82 +103,128 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
   }
 }
 
+// One non-empty row q of a plane: accumulate, transform (FFT) and write it.  Every
+// thread of the row group calls it; it ends with the row buffer free again.
+template <int N, bool FFT, int WT>
+__device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const Record *__restrict__ rec,
+                                             const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
+                                             const KernelParams &kp, float2 *__restrict__ orow, const Tw &tw,
+                                             int jt) {
+  using C = RowCfg<N>;
+  constexpr int EPT = C::EPT, TPR = C::TPR;
+  constexpr int NST = num_stages(N, EPT);
+  constexpr int R0 = stage_radix(N, EPT, 0);
+  constexpr int RL = stage_radix(N, EPT, NST - 1);
+  auto smi = [](int i) { return i + i / EPT; };
+  const int W = WT > 0 ? WT : kp.support;
+  float *sre = reinterpret_cast<float *>(srow), *sim = sre + N;  // planar accumulation
+  const int d_lo = min(q, W - 1);
+  if (nonempty)
+    for (int i = jt; i <= d_lo + 1; i += TPR) bnd[i] = off[(b0 + q - d_lo + i) * kColBlocks];
+  zero_row<N>(srow, jt);
+  __syncthreads();
+  if (nonempty) grid_row<N, WT>(sre, sim, rec, bnd, d_lo, kp, jt);
+  __syncthreads();
+  if constexpr (FFT) {
+    float2 v[EPT];
+#pragma unroll
+    for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+        const float sg = ((idx + q) & 1) ? -1.0f : 1.0f;  // centring sign
+        v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
+      }
+    __syncthreads();  // natural-order reads done before the padded writes
+    stage_compute<N, EPT, TPR, 0, 1>(v, jt, tw, 1);
+    middle_stages<N, EPT, TPR, 1, 1>(v, jt, srow, smi, tw, 1);
+    stage_compute<N, EPT, TPR, NST - 1, 1>(v, jt, tw, 1);
+    if (orow && nonempty) {
+#pragma unroll
+      for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)] = v[b * RL + r];
+    }
+  } else {
+    if (orow)
+      for (int i = jt; i < N; i += TPR) orow[i] = make_float2(sre[i], sim[i]);
+  }
+  __syncthreads();  // the row buffer is reused by the next row
+}
+
+constexpr int kRowBatch = 32;  // rows handed out per counter fetch (one row per CTA step)
+
 template <int N, bool FFT, int WT>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
 k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int np,
             KernelParams kp, float2 *__restrict__ out, uint8_t *__restrict__ occ,
             unsigned long long *__restrict__ counter, Tw tw) {
   using C = RowCfg<N>;
-  constexpr int EPT = C::EPT, TPR = C::TPR, RPC = C::RPC;
-  constexpr int NST = num_stages(N, EPT);
-  constexpr int R0 = stage_radix(N, EPT, 0);
-  constexpr int RL = stage_radix(N, EPT, NST - 1);
+  constexpr int TPR = C::TPR, RPC = C::RPC;
   extern __shared__ __align__(16) float2 sm_rows[];
   __shared__ long long s_item;
   __shared__ uint32_t s_bnd[RPC][kMaxSupport + 2];
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
-  auto smi = [](int i) { return i + i / EPT; };
   const long long total = (long long)np * N;
   const int W = WT > 0 ? WT : kp.support;
-  while (true) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)RPC);
-    __syncthreads();
-    const long long base = s_item;
-    __syncthreads();
-    if (base >= total) break;
-    const long long item = base + rl;
-    const bool valid = item < total;
-    const int pl = valid ? (int)(item / N) : 0;
-    const int q = valid ? (int)(item % N) : 0;
-    const int64_t b0 = (int64_t)(p0 + pl) * N;
-    const bool empty = !valid || off[(b0 + max(0, q - W + 1)) * kColBlocks] == off[(b0 + q + 1) * kColBlocks];
-    float2 *orow = out + ((int64_t)pl * N + q) * N;
-    if (valid && jt == 0) occ[(int64_t)pl * N + q] = empty ? 0 : 1;
-    if constexpr (RPC == 1) {
-      if (empty) {  // uniform across the CTA: one row per step
-        // the column pass reads only occupied rows (occ), so transformed empty rows are
-        // not written; plain gridding hands the planes to the caller and writes zeros
-        if constexpr (!FFT) {
-          float4 *o4 = reinterpret_cast<float4 *>(orow);
-          for (int i = jt; i < N / 2; i += TPR) o4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
-        continue;
+  auto row_empty = [&](long long item) {
+    const int64_t b0 = (int64_t)(p0 + item / N) * N;
+    const int q = (int)(item % N);
+    return off[(b0 + max(0, q - W + 1)) * kColBlocks] == off[(b0 + q + 1) * kColBlocks];
+  };
+  if constexpr (RPC == 1) {
+    // batches of kRowBatch rows: warp 0 finds the non-empty ones (and fills occ), the
+    // CTA then grids and transforms only those; the next batch is fetched meanwhile
+    __shared__ int s_list[kRowBatch], s_cnt;
+    unsigned long long next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(counter, (unsigned long long)kRowBatch);
+    while (true) {
+      if (threadIdx.x == 0) {
+        s_item = (long long)next;
+        next = atomicAdd(counter, (unsigned long long)kRowBatch);
+      }
+      __syncthreads();
+      const long long base = s_item;
+      if (base >= total) break;
+      if (threadIdx.x < 32) {
+        const long long item = base + threadIdx.x;
+        const bool valid = item < total;
+        const bool nonempty = valid && !row_empty(item);
+        if (valid) occ[item] = nonempty ? 1 : 0;
+        // plain gridding hands the planes to the caller: it also lists the empty rows,
+        // which get zeros; the column pass reads only occupied rows of transformed planes
+        const bool listed = FFT ? nonempty : valid;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, listed);
+        if (listed) s_list[__popc(m & ((1u << threadIdx.x) - 1u))] = threadIdx.x * 2 + (nonempty ? 1 : 0);
+        if (threadIdx.x == 0) s_cnt = __popc(m);
+      }
+      __syncthreads();
+      const int cnt = s_cnt;
+      for (int k = 0; k < cnt; ++k) {
+        const int e = s_list[k];
+        const long long item = base + (e >> 1);
+        const int pl = (int)(item / N), q = (int)(item % N);
+        grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
+                                 out + ((int64_t)pl * N + q) * N, tw, jt);
       }
     }
-    float *sre = reinterpret_cast<float *>(srow), *sim = sre + N;  // planar accumulation
-    const int d_lo = min(q, W - 1);
-    if (!empty)
-      for (int i = jt; i <= d_lo + 1; i += TPR) s_bnd[rl][i] = off[(b0 + q - d_lo + i) * kColBlocks];
-    zero_row<N>(srow, jt);
-    __syncthreads();
-    if (!empty) grid_row<N, WT>(sre, sim, rec, s_bnd[rl], d_lo, kp, jt);
-    __syncthreads();
-    if constexpr (FFT) {
-      float2 v[EPT];
-#pragma unroll
-      for (int b = 0; b < EPT / R0; ++b)
-#pragma unroll
-        for (int r = 0; r < R0; ++r) {
-          const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
-          const float sg = ((idx + q) & 1) ? -1.0f : 1.0f;  // centring sign
-          v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
-        }
-      __syncthreads();  // natural-order reads done before the padded writes
-      stage_compute<N, EPT, TPR, 0, 1>(v, jt, tw, 1);
-      middle_stages<N, EPT, TPR, 1, 1>(v, jt, srow, smi, tw, 1);
-      stage_compute<N, EPT, TPR, NST - 1, 1>(v, jt, tw, 1);
-      if (valid && !empty) {
-#pragma unroll
-        for (int b = 0; b < EPT / RL; ++b)
-#pragma unroll
-          for (int r = 0; r < RL; ++r) orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)] = v[b * RL + r];
-      }
-    } else {
-      if (valid)
-        for (int i = jt; i < N; i += TPR) orow[i] = make_float2(sre[i], sim[i]);
+  } else {
+    while (true) {
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)RPC);
+      __syncthreads();
+      const long long base = s_item;
+      __syncthreads();
+      if (base >= total) break;
+      const long long item = base + rl;
+      const bool valid = item < total;
+      const int pl = valid ? (int)(item / N) : 0;
+      const int q = valid ? (int)(item % N) : 0;
+      const bool empty = !valid || row_empty(item);
+      if (valid && jt == 0) occ[item] = empty ? 0 : 1;
+      float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
+      grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, tw, jt);
     }
-    __syncthreads();  // the row buffer is reused by the next step
   }
 }
 

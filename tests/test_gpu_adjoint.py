@@ -42,7 +42,7 @@ def case(n=128, n_vis=2000, seed=0, fov=0.1):
 
 
 @pytest.mark.parametrize("n,n_w,chunk,correct", [(128, 4, 0, True), (128, 4, 3, False), (256, 3, 1, True),
-                                                 (64, 1, 0, True)])
+                                                 (64, 1, 0, True), (2048, 2, 0, True), (16384, 2, 1, False)])
 def test_degrid_matches_oracle(wst, n, n_w, chunk, correct):
     u, v, w, vis, wt, rng = case(n=n, seed=n + n_w)
     cfg = wst.Config(n=n, fov=0.1, n_w=n_w, w_min=-200.0, w_max=200.0, planes_per_chunk=chunk)
@@ -117,8 +117,9 @@ def test_autograd_gradcheck_finite_differences(wst):
                                     nondet_tol=1e-4)
 
 
-def test_kernel_grad_matches_oracle(wst):
-    n, W = 128, 8
+@pytest.mark.parametrize("n", [128, 2048])
+def test_kernel_grad_matches_oracle(wst, n):
+    W = 8
     L = W * 32 + 1
     u, v, w, vis, wt, rng = case(n=n, n_vis=1500, seed=10)
     xs = np.linspace(-W / 2, W / 2, L)

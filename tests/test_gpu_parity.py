@@ -166,7 +166,7 @@ def test_w_range_from_data(wst):
 # K-G: gridded planes
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,W", [(64, 7), (256, 7), (256, 8), (512, 5)])
+@pytest.mark.parametrize("n,W", [(64, 7), (256, 7), (256, 8), (512, 5), (4096, 7)])
 def test_grid_planes(wst, n, W):
     u, v, w, vis = make_case(n=n, n_vis=4000, seed=n + W)
     wt = np.random.default_rng(1).uniform(0.5, 2.0, u.size).astype(np.float32)
@@ -218,7 +218,7 @@ def test_fft_correct_staged(wst, n):
 
 @pytest.mark.parametrize("n,n_w,chunk,flags", [
     (256, 8, 0, 1), (256, 8, 3, 1), (256, 8, 3, 0), (512, 5, 2, 1), (1024, 4, 0, 3), (64, 1, 0, 1),
-    (4096, 2, 1, 1),
+    (4096, 2, 1, 1), (2048, 3, 0, 1), (8192, 2, 1, 1),
 ])
 def test_image_end_to_end(wst, n, n_w, chunk, flags):
     u, v, w, vis = make_case(n=n, n_vis=4000, seed=7 * n + n_w)
