@@ -300,6 +300,24 @@ __device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 y) {
   s.y = ty;
 }
 
+// float-float screen from a cached t = n - 1 (t.x is NaN outside the unit sphere)
+template <bool STEP>
+__device__ __forceinline__ void screen_from_t(const ScreenCtx &sc, float2 t2, int P, int img, float scale,
+                                              float2 &scr, float2 &stp) {
+  scr = make_float2(0.0f, 0.0f);
+  if (STEP) stp = make_float2(0.0f, 0.0f);
+  if (isnan(t2.x)) return;
+  const ff t = {t2.x, t2.y};
+  const float2 w = sc.wc[P];
+  scr = cis_cycles_ff(ff_mul({w.x, w.y}, t));
+  if (STEP) {
+    const float2 dw = sc.dwff[img];
+    stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
+  }
+  scr.x *= scale;
+  scr.y *= scale;
+}
+
 // epilogue modes
 enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
 
@@ -342,6 +360,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   __shared__ float2 sm[LA * C::PADW];
   __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
   __shared__ float2 s_step[EPT][C::THREADS];  // per-plane screen step of each output (thread-private)
+  __shared__ float2 s_nm1[FP64S ? 1 : EPT][C::THREADS];  // n - 1 of each output, float-float
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
@@ -379,8 +398,21 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
             const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
             const float sg = ((kq + kp) & 1) ? -1.0f : 1.0f;
             float2 &st = s_step[b * RL + r][threadIdx.x];
-            if (P == pstart) screen_anchor<FP64S, true>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
-            else screen_anchor<FP64S, false>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
+            if constexpr (FP64S) {
+              if (P == pstart) screen_anchor<true, true>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
+              else screen_anchor<true, false>(sc, kp, kq, P, img, sg, scr[b * RL + r], st);
+            } else {
+              // n - 1 depends on the pixel only: evaluated at the image's first plane
+              float2 &t2 = s_nm1[b * RL + r][threadIdx.x];
+              if (P == pstart) {
+                bool valid;
+                const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+                t2 = valid ? make_float2(t.hi, t.lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+                screen_from_t<true>(sc, t2, P, img, sg, scr[b * RL + r], st);
+              } else {
+                screen_from_t<false>(sc, t2, P, img, sg, scr[b * RL + r], st);
+              }
+            }
           }
       }
       const float2 *tile = stage_buf[(P - p0) & 1];
