@@ -242,6 +242,113 @@ k_cols_a(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ 
     }
 }
 
+// 16-byte asynchronous global -> shared copies (sm_80+ LDGSTS), grouped per plane
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Persistent form of pass CA for the long columns: each CTA walks tiles (plane, a,
+// 16-column band) in band-fastest order; the next tile's rows are copied into a
+// shared staging buffer (cp.async; rows the gridder left empty are zero-filled instead
+// of read) while the current one is transformed, and the stage twiddles, identical for
+// every tile, stay in registers.
+template <int LB, int DIR, bool TW_FIRST>
+__global__ void __launch_bounds__(ColCfg<LB>::THREADS, 1024 / ColCfg<LB>::THREADS)
+k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
+  using C = ColCfg<LB>;
+  constexpr int EPT = C::EPT, TPL = C::TPL;
+  constexpr int NST = num_stages(LB, EPT);
+  constexpr int R0 = stage_radix(LB, EPT, 0);
+  constexpr int RL = stage_radix(LB, EPT, NST - 1);
+  constexpr int PIECES = LB * (kCB / 2);  // 16-byte pieces per tile
+  __shared__ float2 sm[LB * C::PADW];
+  __shared__ __align__(16) float2 stage[2][LB * kCB];
+  const int A = n / LB;
+  // tile t -> band = t mod bands, a = (t / bands) mod A, plane z = t / (bands A); all
+  // powers of two, so shifts and masks (no integer division in the loop)
+  const int lg_bands = 31 - __clz(n / kCB), lg_A = 31 - __clz(A);
+  const int total = nplanes << (lg_bands + lg_A);
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  auto smi = [col](int i) { return i * C::PADW + col; };
+  float2 twr[total_tw_count<LB, EPT>() > 0 ? total_tw_count<LB, EPT>() : 1];
+  all_twiddles<LB, EPT, TPL, DIR>(twr, jt, tw, A);
+  const size_t rstride = (size_t)A * n;  // line element i -> row a + A*i
+  constexpr int PPT = PIECES / C::THREADS;  // pieces per thread (4)
+  static_assert(PIECES % C::THREADS == 0, "pieces");
+  // occupancy of the rows of this thread's pieces, loaded one tile ahead of their use
+  auto load_flags = [&](int t, bool (&f)[PPT]) {
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int i = (threadIdx.x + k * C::THREADS) / (kCB / 2);
+      f[k] = t >= total || !occ || occ[(size_t)z * n + a + A * i];
+    }
+  };
+  auto issue = [&](int t, float2 *buf, const bool (&f)[PPT]) {
+    const int band = t & ((1 << lg_bands) - 1);
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+    const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * kCB;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int c = threadIdx.x + k * C::THREADS;
+      const int i = c / (kCB / 2), part = c % (kCB / 2);
+      if (f[k])
+        cp_async16(sbuf + (uint32_t)(i * kCB + 2 * part) * 8u, src + i * rstride + 2 * part);
+      else
+        reinterpret_cast<float4 *>(buf)[(i * kCB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  };
+  int t = blockIdx.x;
+  bool f0[PPT], f1[PPT];
+  load_flags(t, f0);
+  load_flags(t + gridDim.x, f1);
+  if (t < total) issue(t, stage[0], f0);
+  cp_async_commit();
+  for (int it = 0; t < total; ++it, t += gridDim.x) {
+    if (t + gridDim.x < total) issue(t + gridDim.x, stage[(it + 1) & 1], f1);
+    cp_async_commit();
+    load_flags(t + 2 * (int)gridDim.x, f1);  // consumed by the next iteration's copies
+    cp_async_wait<1>();
+    __syncthreads();
+    const int band = t & ((1 << lg_bands) - 1);
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+    const float2 *buf = stage[it & 1];
+    float2 v[EPT];
+#pragma unroll
+    for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+      for (int rr = 0; rr < R0; ++rr) {
+        const int i = in_index<LB, EPT, TPL, 0>(jt, b, rr);
+        float2 x = buf[i * kCB + col];
+        if (TW_FIRST) x = cmul(x, twiddle(tw, a * i, DIR));
+        v[b * R0 + rr] = x;
+      }
+    stage_compute_pre<LB, EPT, 0, DIR>(v, twr);
+    if constexpr (NST > 1) {
+      middle_stages_pre<LB, EPT, TPL, 1, DIR>(v, jt, sm, smi, twr);
+      stage_compute_pre<LB, EPT, NST - 1, DIR>(v, twr);
+    }
+    float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * kCB + col;
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int rr = 0; rr < RL; ++rr) {
+        const int c = out_index<LB, EPT, TPL, NST - 1>(jt, b, rr);
+        float2 x = v[b * RL + rr];
+        if (!TW_FIRST) x = cmul(x, twiddle(tw, a * c, DIR));
+        dst[(size_t)c * rstride] = x;
+      }
+    __syncthreads();  // staging buffer and shared memory reused
+  }
+  cp_async_wait<0>();
+}
+
 // ---------------------------------------------------------------------------------
 // phase screen helpers (K-P)
 //
@@ -252,7 +359,7 @@ k_cols_a(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ 
 // are the first plane of an image in a chunk and every kAnchor-th plane after it, so
 // the rounding of the recurrence never compounds over more than kAnchor - 1 products.
 // ---------------------------------------------------------------------------------
-constexpr int kAnchor = 8;
+constexpr int kAnchor = 16;
 
 struct ScreenCtx {
   const float2 *l2ff;      // l_a^2 float-float
@@ -325,16 +432,6 @@ enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
 // pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then the centring sign and
 // the screen, and the (Kahan-compensated) sum over the chunk's planes of each image.
 // ---------------------------------------------------------------------------------
-// 16-byte asynchronous global -> shared copies (sm_80+ LDGSTS), grouped per plane
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // The tile of plane P (rows A c .. A c + A - 1, 16 columns) is copied into one of two
 // shared staging buffers while the previous plane is transformed, so the strided loads
 // of the tile never stall the FFT.
@@ -621,8 +718,21 @@ cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool p
 
 template <int LB, int DIR, bool TWF>
 static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes, const uint8_t *occ) {
-  dim3 grd(p->n / kCB, p->n / LB, nplanes);
-  k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ);
+  if constexpr (LB >= 32) {  // persistent, staged
+    auto kern = k_cols_a_pers<LB, DIR, TWF>;
+    int per_sm = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ColCfg<LB>::THREADS, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)nplanes * (p->n / LB) * (p->n / kCB);
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > tiles) grid = tiles;
+    kern<<<(unsigned)grid, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ, nplanes);
+  } else {
+    dim3 grd(p->n / kCB, p->n / LB, nplanes);
+    k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ);
+  }
   return cudaGetLastError();
 }
 
