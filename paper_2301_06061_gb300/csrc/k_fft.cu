@@ -189,12 +189,12 @@ k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long
 // ---------------------------------------------------------------------------------
 constexpr int kCB = 16;  // columns per band (128 bytes per row segment)
 
-template <int L>
+template <int L, int CB = kCB>
 struct ColCfg {
   static constexpr int EPT = L >= 8 ? 8 : L;
   static constexpr int TPL = L / EPT;
-  static constexpr int THREADS = TPL * kCB;
-  static constexpr int PADW = kCB + 1;  // smem row stride (float2)
+  static constexpr int THREADS = TPL * CB;
+  static constexpr int PADW = CB + 1;  // smem row stride (float2)
 };
 
 template <int LB, int DIR, bool TW_FIRST>
@@ -253,27 +253,27 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Persistent form of pass CA for the long columns: each CTA walks tiles (plane, a,
-// 16-column band) in band-fastest order; the next tile's rows are copied into a
+// CB-column band; 32 columns = 256-byte row segments) in band-fastest order; the next tile's rows are copied into a
 // shared staging buffer (cp.async; rows the gridder left empty are zero-filled instead
 // of read) while the current one is transformed, and the stage twiddles, identical for
 // every tile, stay in registers.
-template <int LB, int DIR, bool TW_FIRST>
-__global__ void __launch_bounds__(ColCfg<LB>::THREADS, 1024 / ColCfg<LB>::THREADS)
+template <int LB, int DIR, bool TW_FIRST, int CB>
+__global__ void __launch_bounds__(ColCfg<LB, CB>::THREADS, 1024 / ColCfg<LB, CB>::THREADS)
 k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
-  using C = ColCfg<LB>;
+  using C = ColCfg<LB, CB>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LB, EPT);
   constexpr int R0 = stage_radix(LB, EPT, 0);
   constexpr int RL = stage_radix(LB, EPT, NST - 1);
-  constexpr int PIECES = LB * (kCB / 2);  // 16-byte pieces per tile
+  constexpr int PIECES = LB * (CB / 2);  // 16-byte pieces per tile
   __shared__ float2 sm[LB * C::PADW];
-  __shared__ __align__(16) float2 stage[2][LB * kCB];
+  __shared__ __align__(16) float2 stage[2][LB * CB];
   const int A = n / LB;
   // tile t -> band = t mod bands, a = (t / bands) mod A, plane z = t / (bands A); all
   // powers of two, so shifts and masks (no integer division in the loop)
-  const int lg_bands = 31 - __clz(n / kCB), lg_A = 31 - __clz(A);
+  const int lg_bands = 31 - __clz(n / CB), lg_A = 31 - __clz(A);
   const int total = nplanes << (lg_bands + lg_A);
-  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int col = threadIdx.x % CB, jt = threadIdx.x / CB;
   auto smi = [col](int i) { return i * C::PADW + col; };
   float2 twr[total_tw_count<LB, EPT>() > 0 ? total_tw_count<LB, EPT>() : 1];
   all_twiddles<LB, EPT, TPL, DIR>(twr, jt, tw, A);
@@ -285,23 +285,23 @@ k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restri
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-      const int i = (threadIdx.x + k * C::THREADS) / (kCB / 2);
+      const int i = (threadIdx.x + k * C::THREADS) / (CB / 2);
       f[k] = t >= total || !occ || occ[(size_t)z * n + a + A * i];
     }
   };
   auto issue = [&](int t, float2 *buf, const bool (&f)[PPT]) {
     const int band = t & ((1 << lg_bands) - 1);
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
-    const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * kCB;
+    const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * CB;
     const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int c = threadIdx.x + k * C::THREADS;
-      const int i = c / (kCB / 2), part = c % (kCB / 2);
+      const int i = c / (CB / 2), part = c % (CB / 2);
       if (f[k])
-        cp_async16(sbuf + (uint32_t)(i * kCB + 2 * part) * 8u, src + i * rstride + 2 * part);
+        cp_async16(sbuf + (uint32_t)(i * CB + 2 * part) * 8u, src + i * rstride + 2 * part);
       else
-        reinterpret_cast<float4 *>(buf)[(i * kCB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        reinterpret_cast<float4 *>(buf)[(i * CB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   };
   int t = blockIdx.x;
@@ -325,7 +325,7 @@ k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restri
 #pragma unroll
       for (int rr = 0; rr < R0; ++rr) {
         const int i = in_index<LB, EPT, TPL, 0>(jt, b, rr);
-        float2 x = buf[i * kCB + col];
+        float2 x = buf[i * CB + col];
         if (TW_FIRST) x = cmul(x, twiddle(tw, a * i, DIR));
         v[b * R0 + rr] = x;
       }
@@ -334,7 +334,7 @@ k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restri
       middle_stages_pre<LB, EPT, TPL, 1, DIR>(v, jt, sm, smi, twr);
       stage_compute_pre<LB, EPT, NST - 1, DIR>(v, twr);
     }
-    float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * kCB + col;
+    float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * CB + col;
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
@@ -718,17 +718,18 @@ cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool p
 
 template <int LB, int DIR, bool TWF>
 static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes, const uint8_t *occ) {
-  if constexpr (LB >= 32) {  // persistent, staged
-    auto kern = k_cols_a_pers<LB, DIR, TWF>;
+  if constexpr (LB >= 32) {  // persistent, staged, 32-column bands
+    constexpr int CB = 32;
+    auto kern = k_cols_a_pers<LB, DIR, TWF, CB>;
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ColCfg<LB>::THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ColCfg<LB, CB>::THREADS, 0);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)nplanes * (p->n / LB) * (p->n / kCB);
+    const long long tiles = (long long)nplanes * (p->n / LB) * (p->n / CB);
     long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
     if (grid > tiles) grid = tiles;
-    kern<<<(unsigned)grid, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ, nplanes);
+    kern<<<(unsigned)grid, ColCfg<LB, CB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ, nplanes);
   } else {
     dim3 grd(p->n / kCB, p->n / LB, nplanes);
     k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ);

@@ -201,19 +201,13 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
         }
       }
     }
-    // warp-aggregated histogram: one atomic per distinct key in the warp
+    // warp-aggregated histogram: one reduction (no return value) per distinct key in the warp
     const unsigned active = __ballot_sync(0xFFFFFFFFu, kept);
-    uint32_t rank = 0;
     if (kept) {
       const unsigned peers = __match_any_sync(active, key);
-      const int leader = __ffs(peers) - 1;
-      const int lane = threadIdx.x & 31;
-      uint32_t base_rank = 0;
-      if (lane == leader) base_rank = atomicAdd(&offsets[key], (uint32_t)__popc(peers));
-      base_rank = __shfl_sync(peers, base_rank, leader);
-      rank = base_rank + __popc(peers & ((1u << lane) - 1u));
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&offsets[key], (uint32_t)__popc(peers));
     }
-    if (in) keyinfo[j] = make_uint4(key, rank, xpack, ypack);
+    if (in) keyinfo[j] = make_uint4(key, 0u, xpack, ypack);
     warp_count(&counters[CNT_KEPT], kept);
     warp_count(&counters[CNT_DROPPED], dropped);
     warp_count(&counters[CNT_NONFINITE], nonfinite);
@@ -315,40 +309,53 @@ static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cuda
   return cudaGetLastError();
 }
 
-// pass 2: scatter records to their sorted position (kScatterIlp visibilities in flight
-// per thread: the loads of the key, its bucket offset and the value are independent
-// across them)
+// pass 2: scatter records to their sorted position.  A visibility's position is its
+// bucket's cursor, advanced by a warp-aggregated atomic (one per distinct key in the
+// warp); kScatterIlp visibilities are in flight per thread, their loads and atomics
+// issued before any result is used.  The order inside a bucket is not specified.
 constexpr int kScatterIlp = 4;
 
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
-                          const uint4 *__restrict__ keyinfo, const uint32_t *__restrict__ offsets,
-                          int64_t n_vis, Record *__restrict__ records) {
+                          const uint4 *__restrict__ keyinfo, uint32_t *__restrict__ cursor, int64_t n_vis,
+                          Record *__restrict__ records) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n_vis; j0 += stride * kScatterIlp) {
+  const int lane = threadIdx.x & 31;
+  // uniform trip count across the warp (warp-level votes below)
+  const int64_t start = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t w0 = start; w0 < n_vis; w0 += stride * kScatterIlp) {
     uint4 ki[kScatterIlp];
 #pragma unroll
     for (int h = 0; h < kScatterIlp; ++h) {
-      const int64_t j = j0 + h * stride;
+      const int64_t j = w0 + h * stride + lane;
       ki[h] = j < n_vis ? keyinfo[j] : make_uint4(kDropKey, 0u, 0u, 0u);
     }
-    uint32_t pos[kScatterIlp];
+    uint32_t base[kScatterIlp], peers[kScatterIlp];
+#pragma unroll
+    for (int h = 0; h < kScatterIlp; ++h) {
+      const bool kept = ki[h].x != kDropKey;
+      const unsigned active = __ballot_sync(0xFFFFFFFFu, kept);
+      peers[h] = kept ? __match_any_sync(active, ki[h].x) : 0u;
+      base[h] = (kept && lane == __ffs(peers[h]) - 1) ? atomicAdd(&cursor[ki[h].x], (uint32_t)__popc(peers[h])) : 0u;
+    }
     float2 val[kScatterIlp];
     float wt[kScatterIlp];
 #pragma unroll
     for (int h = 0; h < kScatterIlp; ++h) {
-      const int64_t j = j0 + h * stride;
+      const int64_t j = w0 + h * stride + lane;
       if (ki[h].x != kDropKey) {
-        pos[h] = offsets[ki[h].x] + ki[h].y;
         val[h] = vis[j];
         wt[h] = weight ? weight[j] : 1.0f;
       }
     }
 #pragma unroll
     for (int h = 0; h < kScatterIlp; ++h) {
-      if (ki[h].x == kDropKey) continue;
-      uint4 *dst = reinterpret_cast<uint4 *>(records + pos[h]);
+      const bool kept = ki[h].x != kDropKey;
+      const uint32_t b = __shfl_sync(0xFFFFFFFFu, base[h], kept ? __ffs(peers[h]) - 1 : lane);
+      if (!kept) continue;
+      const uint32_t pos = b + __popc(peers[h] & ((1u << lane) - 1u));
+      uint4 *dst = reinterpret_cast<uint4 *>(records + pos);
       dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(val[h].x * wt[h]), __float_as_uint(val[h].y * wt[h]));
-      dst[1] = make_uint4((uint32_t)(j0 + h * stride), __float_as_uint(wt[h]), 0u, 0u);
+      dst[1] = make_uint4((uint32_t)(w0 + h * stride + lane), __float_as_uint(wt[h]), 0u, 0u);
     }
   }
 }
@@ -396,8 +403,9 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   p->launches += 1;
   if ((e = cudaGetLastError())) return e;
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
-  k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(
-      vis, weight, ws.keyinfo, ws.offsets, p->n_vis, ws.records);
+  if ((e = cudaMemcpyAsync(ws.cursor, ws.offsets, sizeof(uint32_t) * nb1, cudaMemcpyDeviceToDevice, s))) return e;
+  k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(vis, weight, ws.keyinfo, ws.cursor, p->n_vis,
+                                                              ws.records);
   p->launches += 1;
   return cudaGetLastError();
 }

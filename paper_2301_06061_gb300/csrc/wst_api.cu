@@ -43,7 +43,7 @@ int ilog2(int x) {
 }
 
 struct Layout {
-  size_t keyinfo_planes, records, offsets, scan_tmp, counters, wminmax, occ, comp, total;
+  size_t keyinfo_planes, records, offsets, cursor, scan_tmp, counters, wminmax, occ, comp, total;
 };
 
 Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
@@ -56,6 +56,8 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   L.records = off;
   off += align_up((size_t)n_vis * sizeof(Record));
   L.offsets = off;
+  off += align_up((size_t)(p->n_buckets + 1) * sizeof(uint32_t));
+  L.cursor = off;
   off += align_up((size_t)(p->n_buckets + 1) * sizeof(uint32_t));
   L.scan_tmp = off;
   off += align_up((size_t)scan_tmp_words(p->n_buckets + 1) * sizeof(uint32_t));
@@ -275,6 +277,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.planes = (float2 *)(p->ws + L.keyinfo_planes);
   W.records = (Record *)(p->ws + L.records);
   W.offsets = (uint32_t *)(p->ws + L.offsets);
+  W.cursor = (uint32_t *)(p->ws + L.cursor);
   W.scan_tmp = (uint32_t *)(p->ws + L.scan_tmp);
   W.counters = (unsigned long long *)(p->ws + L.counters);
   W.wminmax = (uint32_t *)(p->ws + L.wminmax);

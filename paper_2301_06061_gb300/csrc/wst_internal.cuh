@@ -69,9 +69,10 @@ struct KernelParams {
 };
 
 struct Workspace {
-  uint4 *keyinfo;      // per visibility: key, rank, xpack, ypack (aliases the plane buffer)
+  uint4 *keyinfo;      // per visibility: key, 0, xpack, ypack (aliases the plane buffer)
   Record *records;     // sorted records
   uint32_t *offsets;   // bucket offsets [n_buckets + 1]
+  uint32_t *cursor;    // scatter cursors (a copy of the offsets, advanced by the scatter)
   uint32_t *scan_tmp;  // scan partial sums
   unsigned long long *counters;  // CNT_* slots
   uint32_t *wminmax;   // per image: ordered-int min and max of finite w
