@@ -3,6 +3,8 @@
 // stage driver.  (Included by k_fft.cu and k_rowgrid.cu.)
 #pragma once
 
+#include <type_traits>
+
 #include "wst_internal.cuh"
 
 namespace wst {
@@ -189,6 +191,24 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[EPT], int jt, const Tw
   }
 }
 
+// Stage S with the twiddles from a provider: twp(S, b, r, k) is the factor of input r
+// of butterfly b (k = j mod NS), S passed as std::integral_constant.
+template <int L, int EPT, int TPL, int S, int DIR, class TWP>
+__device__ __forceinline__ void stage_compute_f(float2 (&v)[EPT], int jt, const TWP &twp) {
+  constexpr int R = stage_radix(L, EPT, S);
+  constexpr int NS = stage_ns(L, EPT, S);
+#pragma unroll
+  for (int b = 0; b < EPT / R; ++b) {
+    const int j = jt + b * TPL;
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], twp(std::integral_constant<int, S>(), b, r, k));
+    }
+    dft<R, DIR>(&v[b * R]);
+  }
+}
+
 // Twiddles of stage S held in registers, for kernels that run the same transform many
 // times (one per w-plane): twp[b (R - 1) + r - 1] is the factor of input r of butterfly b.
 template <int L, int EPT, int S>
@@ -278,6 +298,30 @@ __device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *
       __syncthreads();  // every load of this stage done before the next stores
       stage_compute<L, EPT, TPL, S, DIR>(v, jt, tw, twscale);
       middle_stages<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, tw, twscale);
+    }
+  }
+}
+
+// middle_stages with the twiddles from a provider (see stage_compute_f)
+template <int L, int EPT, int TPL, int S, int DIR, class SMI, class TWP>
+__device__ __forceinline__ void middle_stages_f(float2 (&v)[EPT], int jt, float2 *sm, SMI smi, const TWP &twp) {
+  constexpr int NST = num_stages(L, EPT);
+  if constexpr (S < NST) {
+    constexpr int RP = stage_radix(L, EPT, S - 1);
+#pragma unroll
+    for (int b = 0; b < EPT / RP; ++b)
+#pragma unroll
+      for (int r = 0; r < RP; ++r) sm[smi(out_index<L, EPT, TPL, S - 1>(jt, b, r))] = v[b * RP + r];
+    __syncthreads();
+    constexpr int R = stage_radix(L, EPT, S);
+#pragma unroll
+    for (int b = 0; b < EPT / R; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = sm[smi(in_index<L, EPT, TPL, S>(jt, b, r))];
+    if constexpr (S + 1 < NST) {
+      __syncthreads();
+      stage_compute_f<L, EPT, TPL, S, DIR>(v, jt, twp);
+      middle_stages_f<L, EPT, TPL, S + 1, DIR>(v, jt, sm, smi, twp);
     }
   }
 }
