@@ -302,6 +302,79 @@ __device__ __forceinline__ void middle_stages(float2 (&v)[EPT], int jt, float2 *
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Shared-memory twiddle tables for kernels that transform many lines of length L with
+// the same (EPT, TPL) layout.  Stage S >= 1 needs w_L^{k r M}, M = L/(NS R), k = j mod
+// NS, j = jt + b TPL.  If NS <= TPL the table is T_S[r - 1][k] (k < NS); otherwise
+// k = jt + (b TPL mod NS) and the table is T_S[r - 1][jt] (jt < TPL) times the constant
+// w_L^{(b TPL mod NS) r M} = e^{2 pi i b' r / Q}, b' = (b TPL mod NS)/TPL,
+// Q = NS R / TPL <= EPT <= 32.  Consecutive threads read consecutive entries (or one
+// broadcast entry): no bank conflicts, no sign logic.  Entries hold the positive
+// exponent; DIR < 0 conjugates.
+// ---------------------------------------------------------------------------------
+template <int L, int EPT, int TPL, int S>
+constexpr int stage_table_size() {
+  if constexpr (S == 0) {
+    return 0;
+  } else {
+    constexpr int R = stage_radix(L, EPT, S), NS = stage_ns(L, EPT, S);
+    return (R - 1) * (NS <= TPL ? NS : TPL);
+  }
+}
+template <int L, int EPT, int TPL, int S>
+constexpr int stage_table_offset() {
+  if constexpr (S == 0) return 0;
+  else return stage_table_offset<L, EPT, TPL, S - 1>() + stage_table_size<L, EPT, TPL, S - 1>();
+}
+template <int L, int EPT, int TPL>
+constexpr int line_table_size() {
+  return stage_table_offset<L, EPT, TPL, num_stages(L, EPT)>();
+}
+
+template <int L, int EPT, int TPL, int S = 1>
+__device__ __forceinline__ void fill_line_tables(float2 *T, const Tw &tw) {
+  if constexpr (S < num_stages(L, EPT)) {
+    constexpr int R = stage_radix(L, EPT, S), NS = stage_ns(L, EPT, S), M = L / (NS * R);
+    constexpr int WD = NS <= TPL ? NS : TPL;
+    float2 *base = T + stage_table_offset<L, EPT, TPL, S>();
+    for (int i = threadIdx.x; i < (R - 1) * WD; i += blockDim.x) base[i] = twiddle(tw, (i % WD) * (i / WD + 1) * M, 1);
+    fill_line_tables<L, EPT, TPL, S + 1>(T, tw);
+  }
+}
+
+// e^{2 pi i e / 32}, e in [0, 32)
+__device__ __forceinline__ float2 root32(int e) {
+  constexpr float c32[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                            0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                            0.19509032201612826785f, 0.0f};
+  const int q = e >> 3, m = e & 7;  // quadrant, position in it
+  const float c = c32[m], s = c32[8 - m];
+  return q == 0 ? make_float2(c, s) : q == 1 ? make_float2(-s, c) : q == 2 ? make_float2(-c, -s) : make_float2(s, -c);
+}
+
+template <int L, int EPT, int TPL, int DIR>
+struct TableTw {
+  const float2 *T;
+  int jt;
+  template <int S>
+  __device__ __forceinline__ float2 operator()(std::integral_constant<int, S>, int b, int r, int k) const {
+    constexpr int R = stage_radix(L, EPT, S), NS = stage_ns(L, EPT, S);
+    const float2 *base = T + stage_table_offset<L, EPT, TPL, S>();
+    float2 w;
+    if constexpr (NS <= TPL) {
+      w = base[(r - 1) * NS + k];
+    } else {
+      constexpr int Q = NS * R / TPL;
+      w = base[(r - 1) * TPL + jt];
+      const int bq = ((b * TPL) % NS) / TPL;
+      const int e = (bq * r * (32 / Q)) & 31;
+      if (e != 0) w = cmul(w, root32(e));
+    }
+    if (DIR < 0) w.y = -w.y;
+    return w;
+  }
+};
+
 // middle_stages with the twiddles from a provider (see stage_compute_f)
 template <int L, int EPT, int TPL, int S, int DIR, class SMI, class TWP>
 __device__ __forceinline__ void middle_stages_f(float2 (&v)[EPT], int jt, float2 *sm, SMI smi, const TWP &twp) {

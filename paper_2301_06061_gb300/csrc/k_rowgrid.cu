@@ -105,27 +105,11 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
 
 // One non-empty row q of a plane: accumulate, transform (FFT) and write it.  Every
 // thread of the row group calls it; it ends with the row buffer free again.
-// Shared-memory twiddle tables of the longest rows (N = 16384, radix 32 32 16), laid
-// out so that a warp's reads are conflict-free and need no sign logic:
-//   stage 1:  T1[r - 1][k]   = e^{2 pi i k r / 1024},   k = lane (j mod 32), r = 1..31
-//   stage 2:  T2[r - 1][jt]  = e^{2 pi i jt r / 16384}, jt < 512, r = 1..15; the butterfly
-//             j = jt + 512 has the extra factor e^{2 pi i r / 32} (a constant).
-constexpr int kT1 = 31 * 32, kT2 = 15 * 512;
-template <int N>
-constexpr bool row_tables() {
-  return N == 16384 && RowCfg<N>::EPT == 32;
-}
-
-__device__ __forceinline__ void fill_row_tables(float2 *t1, float2 *t2, const Tw &tw) {
-  for (int i = threadIdx.x; i < kT1; i += blockDim.x) t1[i] = twiddle(tw, 16 * (i % 32) * (i / 32 + 1), 1);
-  for (int i = threadIdx.x; i < kT2; i += blockDim.x) t2[i] = twiddle(tw, (i % 512) * (i / 512 + 1), 1);
-}
-
 template <int N, bool FFT, int WT>
 __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const Record *__restrict__ rec,
                                              const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
-                                             const KernelParams &kp, float2 *__restrict__ orow, const Tw &tw,
-                                             const float2 *t1, const float2 *t2, int jt) {
+                                             const KernelParams &kp, float2 *__restrict__ orow,
+                                             const float2 *twt, int jt) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -152,30 +136,10 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
         v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
       }
     __syncthreads();  // natural-order reads done before the padded writes
-    if constexpr (row_tables<N>()) {
-      auto twp = [&](auto s, int b, int r, int k) -> float2 {
-        if constexpr (decltype(s)::value == 1) {
-          return t1[(r - 1) * 32 + k];
-        } else {
-          const float2 w = t2[(r - 1) * 512 + (k & 511)];
-          if (b == 0) return w;
-          constexpr float c32[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
-                                    0.83146961230254523708f, 0.70710678118654752440f, 0.55557023301960222474f,
-                                    0.38268343236508977173f, 0.19509032201612826785f, 0.0f};
-          // e^{2 pi i r / 32}, r = 1..15
-          const float c = r <= 8 ? c32[r] : -c32[16 - r];
-          const float sn = r <= 8 ? c32[8 - r] : c32[r - 8];
-          return cmul(w, make_float2(c, sn));
-        }
-      };
-      stage_compute_f<N, EPT, TPR, 0, 1>(v, jt, twp);
-      middle_stages_f<N, EPT, TPR, 1, 1>(v, jt, srow, smi, twp);
-      stage_compute_f<N, EPT, TPR, NST - 1, 1>(v, jt, twp);
-    } else {
-      stage_compute<N, EPT, TPR, 0, 1>(v, jt, tw, 1);
-      middle_stages<N, EPT, TPR, 1, 1>(v, jt, srow, smi, tw, 1);
-      stage_compute<N, EPT, TPR, NST - 1, 1>(v, jt, tw, 1);
-    }
+    const TableTw<N, EPT, TPR, 1> twp{twt, jt};
+    stage_compute_f<N, EPT, TPR, 0, 1>(v, jt, twp);
+    middle_stages_f<N, EPT, TPR, 1, 1>(v, jt, srow, smi, twp);
+    stage_compute_f<N, EPT, TPR, NST - 1, 1>(v, jt, twp);
     if (orow && nonempty) {
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
@@ -203,8 +167,8 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
   __shared__ uint32_t s_bnd[RPC][kMaxSupport + 2];
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
-  float2 *t1 = sm_rows + RPC * C::PADL, *t2 = t1 + kT1;  // row_tables<N>() only
-  if constexpr (row_tables<N>()) fill_row_tables(t1, t2, tw);  // visible after the first barrier
+  float2 *twt = sm_rows + RPC * C::PADL;  // twiddle tables (visible after the first barrier)
+  if constexpr (FFT) fill_line_tables<N, C::EPT, TPR>(twt, tw);
   const long long total = (long long)np * N;
   const int W = WT > 0 ? WT : kp.support;
   auto row_empty = [&](long long item) {
@@ -245,7 +209,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const long long item = base + (e >> 1);
         const int pl = (int)(item / N), q = (int)(item % N);
         grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
-                                 out + ((int64_t)pl * N + q) * N, tw, t1, t2, jt);
+                                 out + ((int64_t)pl * N + q) * N, twt, jt);
       }
     }
   } else {
@@ -262,8 +226,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       const bool empty = !valid || row_empty(item);
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
-      grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, tw, t1, t2,
-                               jt);
+      grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt);
     }
   }
 }
@@ -284,7 +247,9 @@ k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec
   constexpr int RL = stage_radix(N, EPT, NST - 1);
   extern __shared__ __align__(16) float2 sm_rows[];
   __shared__ long long s_item;
-  float *ptab = reinterpret_cast<float *>(sm_rows + RPC * C::PADL);  // KGRAD partial table
+  float2 *twt = sm_rows + RPC * C::PADL;  // twiddle tables (visible after the first barrier)
+  fill_line_tables<N, C::EPT, TPR>(twt, tw);
+  float *ptab = reinterpret_cast<float *>(twt + line_table_size<N, C::EPT, C::TPR>());  // KGRAD partial table
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
   auto smi = [](int i) { return i + i / EPT; };
@@ -314,9 +279,10 @@ k_rows_adjoint(const float2 *__restrict__ planes, const Record *__restrict__ rec
     for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
       for (int r = 0; r < R0; ++r) v[b * R0 + r] = grow[in_index<N, EPT, TPR, 0>(jt, b, r)];
-    stage_compute<N, EPT, TPR, 0, -1>(v, jt, tw, 1);
-    middle_stages<N, EPT, TPR, 1, -1>(v, jt, srow, smi, tw, 1);
-    stage_compute<N, EPT, TPR, NST - 1, -1>(v, jt, tw, 1);
+    const TableTw<N, EPT, TPR, -1> twp{twt, jt};
+    stage_compute_f<N, EPT, TPR, 0, -1>(v, jt, twp);
+    middle_stages_f<N, EPT, TPR, 1, -1>(v, jt, srow, smi, twp);
+    stage_compute_f<N, EPT, TPR, NST - 1, -1>(v, jt, twp);
     __syncthreads();  // every padded read done before the natural-order writes
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
@@ -420,7 +386,7 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
   auto kern = !FFT ? k_grid_rows<N, FFT, 0>
               : p->cfg.support == 7 ? k_grid_rows<N, FFT, 7>
               : p->cfg.support == 8 ? k_grid_rows<N, FFT, 8> : k_grid_rows<N, FFT, 0>;
-  const size_t smem = sizeof(float2) * (C::RPC * C::PADL + (row_tables<N>() ? kT1 + kT2 : 0));
+  const size_t smem = sizeof(float2) * (C::RPC * C::PADL + (FFT ? line_table_size<N, C::EPT, C::TPR>() : 0));
   int grid = 0;
   cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
   if (e != cudaSuccess) return e;
@@ -437,7 +403,8 @@ static cudaError_t launch_rows_adjoint(wst_plan_s *p, int p0, int np, const floa
                                        float *dtab) {
   using C = RowCfg<N>;
   auto kern = k_rows_adjoint<N, KGRAD>;
-  const size_t smem = sizeof(float2) * C::RPC * C::PADL + (KGRAD ? sizeof(float) * p->cfg.ktable_len : 0);
+  const size_t smem = sizeof(float2) * (C::RPC * C::PADL + line_table_size<N, C::EPT, C::TPR>()) +
+                      (KGRAD ? sizeof(float) * p->cfg.ktable_len : 0);
   int grid = 0;
   cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
   if (e != cudaSuccess) return e;
