@@ -342,7 +342,7 @@ k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restri
         const int c = out_index<LB, EPT, TPL, NST - 1>(jt, b, rr);
         float2 x = v[b * RL + rr];
         if (!TW_FIRST) x = cmul(x, twiddle(tw, a * c, DIR));
-        dst[(size_t)c * rstride] = x;
+        __stcs(&dst[(size_t)c * rstride], x);
       }
     __syncthreads();  // staging buffer and shared memory reused
   }

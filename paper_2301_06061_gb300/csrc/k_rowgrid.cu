@@ -144,7 +144,8 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-        for (int r = 0; r < RL; ++r) orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)] = v[b * RL + r];
+        for (int r = 0; r < RL; ++r)  // streaming stores: keep the L2 for the records
+          __stcs(&orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)], v[b * RL + r]);
     }
   } else {
     if (orow)
