@@ -44,6 +44,28 @@ __device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q
       ga *= ra;
       ra *= q;
     }
+  } else if (kp.tap_table) {
+    // tabulated kernel: all W taps share the sub-cell position, so their bracketing
+    // samples are one contiguous run of W pairs (tap-major table)
+    const float pos = gx * (float)kp.per_cell;
+    const int i = min((int)pos, kp.per_cell - 1);
+    const float f = pos - (float)i;
+    const float2 *run = kp.tap_table + (size_t)i * WT;
+    if constexpr (WT % 2 == 0) {  // 16-byte aligned: two taps per load
+      const float4 *run4 = reinterpret_cast<const float4 *>(run);
+#pragma unroll
+      for (int a = 0; a < WT / 2; ++a) {
+        const float4 t = __ldg(run4 + a);
+        g[2 * a] = fmaf(f, t.y - t.x, t.x);
+        g[2 * a + 1] = fmaf(f, t.w - t.z, t.z);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < WT; ++a) {
+        const float2 t = __ldg(run + a);
+        g[a] = fmaf(f, t.y - t.x, t.x);
+      }
+    }
   } else {
 #pragma unroll
     for (int a = 0; a < WT; ++a) g[a] = kernel_eval(kp, (float)a - kp.half + gx);

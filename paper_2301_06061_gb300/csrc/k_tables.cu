@@ -18,7 +18,27 @@ KernelParams kernel_params(const wst_plan_s *p) {
   k.table = p->ktable;
   k.table_len = p->cfg.ktable_len;
   k.table_scale = (k.kind == WST_KERNEL_TABLE) ? (float)((double)(p->cfg.ktable_len - 1) / p->W) : 0.0f;
+  k.tap_table = p->ktap;
+  k.per_cell = p->ktap ? (p->cfg.ktable_len - 1) / p->W : 0;
   return k;
+}
+
+// Tap-major copy of a kernel table with L - 1 = W pc samples: entry [i][a] holds the two
+// samples that bracket tap a at sub-cell position i / pc, so the W taps of one
+// visibility (all at the same sub-cell offset) are one contiguous run of W pairs.
+__global__ void k_tap_table(const float *t, float2 *tap, int W, int pc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= W * pc) return;
+  const int i = idx / W, a = idx % W;
+  tap[idx] = make_float2(t[a * pc + i], t[a * pc + i + 1]);
+}
+
+cudaError_t build_tap_table(wst_plan_s *p) {
+  if (!p->ktap) return cudaSuccess;
+  const int pc = (p->cfg.ktable_len - 1) / p->W;
+  k_tap_table<<<(p->W * pc + 255) / 256, 256, 0, p->stream>>>(p->ktable, p->ktap, p->W, pc);
+  p->launches += 1;
+  return cudaGetLastError();
 }
 
 // half-wave table exp(+2 pi i m / N), m < N/2, rounded once from FP64

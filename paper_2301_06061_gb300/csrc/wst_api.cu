@@ -88,6 +88,7 @@ void destroy_tables(wst_plan_s *p) {
   cudaFree(p->l2ff);
   cudaFree(p->l2d);
   cudaFree(p->ktable);
+  cudaFree(p->ktap);
   cudaFree(p->wrange);
   cudaFree(p->wrange_ff);
   cudaFree(p->wcentre);
@@ -195,6 +196,7 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   ALLOC(p->dwff, c.batch);
   ALLOC(p->batch_off, c.batch + 1);
   if (c.kernel == WST_KERNEL_TABLE) ALLOC(p->ktable, c.ktable_len);
+  if (c.kernel == WST_KERNEL_TABLE && (c.ktable_len - 1) % c.support == 0) ALLOC(p->ktap, c.ktable_len - 1);
 #undef ALLOC
   if (e != cudaSuccess) {
     destroy_tables(p);
@@ -247,6 +249,7 @@ wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
   WST_CUDA(p, cudaMemcpyAsync(p->ktable, table_dev, sizeof(float) * p->cfg.ktable_len,
                               cudaMemcpyDeviceToDevice, p->stream), "table copy");
   WST_CUDA(p, build_correction(p), "correction table");
+  WST_CUDA(p, build_tap_table(p), "tap table");
   p->table_set = true;
   return WST_OK;
 }

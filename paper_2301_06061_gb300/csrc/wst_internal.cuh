@@ -66,6 +66,8 @@ struct KernelParams {
   const float *table;  // TABLE: device samples
   int table_len;
   float table_scale;   // (L-1)/W
+  const float2 *tap_table;  // TABLE with L - 1 = W * per_cell: [per_cell][W] pairs (T[a pc + i], T[a pc + i + 1])
+  int per_cell;
 };
 
 struct Workspace {
@@ -98,6 +100,7 @@ struct wst_plan_s {
   float2 *l2ff = nullptr;    // l_a^2 as float-float
   double *l2d = nullptr;     // l_a^2 in FP64 (WST_FLAG_FP64_SCREEN)
   float *ktable = nullptr;   // TABLE kernel samples
+  float2 *ktap = nullptr;    // TABLE samples in tap-major pairs (see KernelParams::tap_table)
   double *wrange = nullptr;  // per image: w_lo, scale = n_w/(w_hi-w_lo), dw, w_hi
   float4 *wrange_ff = nullptr;  // per image: w_lo and scale as float-float pairs
   float2 *wcentre = nullptr; // per global plane: centre w_k as float-float
@@ -239,6 +242,7 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 namespace wst {
 
 KernelParams kernel_params(const wst_plan_s *p);
+cudaError_t build_tap_table(wst_plan_s *p);
 
 // k_tables.cu
 cudaError_t build_tables(wst_plan_s *p);
