@@ -349,6 +349,102 @@ k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restri
   cp_async_wait<0>();
 }
 
+// Pass CA with 16 elements per thread (LB = 32, 64, 128: radix 16 then LB/16), for the
+// same persistent tile walk: one exchange between the two register stages, made in
+// place in the tile's own staging buffer (a warp covers 32 columns at one line
+// position, so shared-memory accesses are conflict-free without padding and twiddles
+// are warp-uniform), and the factors w_N^{a c} of the tile taken from a shared table
+// filled at the top of each tile.
+template <int LB, int DIR, bool TW_FIRST>
+__global__ void __launch_bounds__(LB / 16 * 32, 768 / (LB / 16 * 32))
+k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
+  constexpr int CB = 32, EPT = 16, TPL = LB / EPT, THREADS = TPL * CB;
+  constexpr int R1 = LB / 16;  // radix of the second stage
+  static_assert(num_stages(LB, EPT) == 2 && stage_radix(LB, EPT, 1) == R1, "two stages");
+  constexpr int PIECES = LB * (CB / 2);     // 16-byte pieces per tile
+  constexpr int PPT = PIECES / THREADS;     // pieces per thread (8)
+  static_assert(PIECES % THREADS == 0, "pieces");
+  __shared__ __align__(16) float2 stage[2][LB * CB];
+  __shared__ float2 s_tw[LB];  // w_N^{DIR a c}, c < LB, for the tile being transformed
+  const int A = n / LB;
+  const int lg_bands = 31 - __clz(n / CB), lg_A = 31 - __clz(A);
+  const int total = nplanes << (lg_bands + lg_A);
+  const int col = threadIdx.x % CB, jt = threadIdx.x / CB;
+  float2 twr[total_tw_count<LB, EPT>()];
+  all_twiddles<LB, EPT, TPL, DIR>(twr, jt, tw, A);
+  const size_t rstride = (size_t)A * n;  // line element i -> row a + A*i
+  auto load_flags = [&](int t, bool (&f)[PPT]) {
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int i = (threadIdx.x + k * THREADS) / (CB / 2);
+      f[k] = t >= total || !occ || occ[(size_t)z * n + a + A * i];
+    }
+  };
+  auto issue = [&](int t, float2 *buf, const bool (&f)[PPT]) {
+    const int band = t & ((1 << lg_bands) - 1);
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+    const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * CB;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int c = threadIdx.x + k * THREADS;
+      const int i = c / (CB / 2), part = c % (CB / 2);
+      if (f[k])
+        cp_async16(sbuf + (uint32_t)(i * CB + 2 * part) * 8u, src + i * rstride + 2 * part);
+      else
+        reinterpret_cast<float4 *>(buf)[(i * CB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  };
+  int t = blockIdx.x;
+  bool f0[PPT], f1[PPT];
+  load_flags(t, f0);
+  load_flags(t + gridDim.x, f1);
+  if (t < total) issue(t, stage[0], f0);
+  cp_async_commit();
+  for (int it = 0; t < total; ++it, t += gridDim.x) {
+    if (t + gridDim.x < total) issue(t + gridDim.x, stage[(it + 1) & 1], f1);
+    cp_async_commit();
+    load_flags(t + 2 * (int)gridDim.x, f1);
+    const int band = t & ((1 << lg_bands) - 1);
+    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
+    if (threadIdx.x < LB) s_tw[threadIdx.x] = twiddle(tw, (a * (int)threadIdx.x) & (n - 1), DIR);
+    cp_async_wait<1>();
+    __syncthreads();
+    float2 *buf = stage[it & 1];
+    float2 v[EPT];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = jt + r * TPL;
+      float2 x = buf[i * CB + col];
+      if (TW_FIRST) x = cmul(x, s_tw[i]);
+      v[r] = x;
+    }
+    dft<16, DIR>(v);
+    __syncthreads();  // every stage-0 load of the tile done before the in-place exchange
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[(16 * jt + r) * CB + col] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 16 / R1; ++b)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[b * R1 + r] = buf[(jt + b * TPL + 16 * r) * CB + col];
+    stage_compute_pre<LB, EPT, 1, DIR>(v, twr);
+    float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * CB + col;
+#pragma unroll
+    for (int b = 0; b < 16 / R1; ++b)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int c = jt + b * TPL + 16 * r;
+        float2 x = v[b * R1 + r];
+        if (!TW_FIRST) x = cmul(x, s_tw[c]);
+        __stcs(&dst[(size_t)c * rstride], x);
+      }
+    __syncthreads();  // staging buffer and twiddle table reused
+  }
+  cp_async_wait<0>();
+}
+
 // ---------------------------------------------------------------------------------
 // phase screen helpers (K-P)
 //
@@ -442,6 +538,47 @@ __device__ __forceinline__ void stage_tile_async(float2 *buf, const float2 *plan
   for (int i = threadIdx.x; i < CHUNKS; i += ColCfg<LA>::THREADS) {
     const int row = i / (kCB / 2), part = i % (kCB / 2);
     cp_async16(sbuf + (uint32_t)(row * kCB + 2 * part) * 8u, plane + (size_t)(row0 + row) * n + col0 + 2 * part);
+  }
+}
+
+// Tile copy for THREADS threads (16-byte pieces, LA rows of kCB columns).
+template <int LA, int THREADS>
+__device__ __forceinline__ void stage_tile_async16(float2 *buf, const float2 *plane, int n, int row0, int col0) {
+  constexpr int CHUNKS = LA * (kCB / 2);
+  static_assert(CHUNKS % THREADS == 0, "pieces");
+  const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll
+  for (int k = 0; k < CHUNKS / THREADS; ++k) {
+    const int i = threadIdx.x + k * THREADS;
+    const int row = i / (kCB / 2), part = i % (kCB / 2);
+    cp_async16(sbuf + (uint32_t)(row * kCB + 2 * part) * 8u, plane + (size_t)(row0 + row) * n + col0 + 2 * part);
+  }
+}
+
+// Write one pixel's plane sum (s, compensation cmp) of a chunk: merged with the running
+// (sum, compensation) of earlier chunks unless the image's first plane is in this chunk,
+// and finished (compensation folded in, grid correction f applied) if its last plane is.
+__device__ __forceinline__ void flush_pixel(float2 *im, float2 *cp, size_t o, float2 sum, float2 cmp,
+                                            bool first_any, bool last_any, int flags, float f) {
+  if (flags & ACC_STAGED) {
+    im[o] = cadd(im[o], csub(sum, cmp));
+    return;
+  }
+  if (!first_any) {
+    float2 acc_s = im[o];
+    float2 acc_c = cp ? cp[o] : make_float2(0.0f, 0.0f);
+    kahan_add(acc_s, acc_c, sum);
+    kahan_add(acc_s, acc_c, make_float2(-cmp.x, -cmp.y));
+    sum = acc_s;
+    cmp = acc_c;
+  }
+  if (last_any) {
+    float2 out = csub(sum, cmp);
+    if (flags & ACC_CORRECT) out = make_float2(out.x * f, out.y * f);
+    im[o] = out;
+  } else {
+    im[o] = sum;
+    if (cp) cp[o] = cmp;
   }
 }
 
@@ -569,6 +706,130 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
           im[o] = sum;
           if (cp) cp[o] = cmp;
         }
+      }
+  }
+}
+
+// Pass CB + K-P with 16 elements per thread for LA = 64, 128 (radix 16, then LA/16):
+// one exchange per plane, made in place in the plane's staging buffer (each half-warp
+// covers the 16 columns at one line position), so a plane costs four barriers for 16
+// outputs per thread.  Screen, Kahan sum and flush as in k_cols_b_acc.
+template <int LA, bool FP64S>
+__global__ void __launch_bounds__(LA / 16 * kCB, LA == 128 ? 3 : 6)
+k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
+           int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
+  constexpr int EPT = 16, TPL = LA / EPT, THREADS = TPL * kCB, R1 = LA / 16;
+  static_assert(num_stages(LA, EPT) == 2 && stage_radix(LA, EPT, 1) == R1, "two stages");
+  __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
+  static_assert(EPT * THREADS <= LA * kCB, "anchor screens fit a staging buffer");
+  __shared__ float2 s_step[EPT][THREADS];                  // per-plane screen step of each output
+  __shared__ float2 s_nm1[FP64S ? 1 : EPT][THREADS];       // n - 1 of each output, float-float
+  const int B = n / LA;
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int c = blockIdx.y;
+  const int col0 = blockIdx.x * kCB;
+  const int kp = col0 + col;
+  const bool kahan = flags & ACC_KAHAN;
+  const size_t plane_elems = (size_t)n * n;
+  // stage-1 twiddles (one list per line position jt, read as half-warp broadcasts)
+  constexpr int NTW = total_tw_count<LA, EPT>();
+  __shared__ float2 s_tw1[NTW][TPL];
+  if (threadIdx.x < TPL) {
+    float2 twr[NTW];
+    all_twiddles<LA, EPT, TPL, 1>(twr, threadIdx.x, tw, B);
+#pragma unroll
+    for (int i = 0; i < NTW; ++i) s_tw1[i][threadIdx.x] = twr[i];
+  }
+  // output e = b R1 + r of this thread is line element jt + b TPL + 16 r, image row c + B (that)
+  auto out_row = [&](int b, int r) { return c + B * (jt + b * TPL + 16 * r); };
+  stage_tile_async16<LA, THREADS>(stage_buf[0], planes, n, LA * c, col0);
+  cp_async_commit();
+  int P = p0;
+  while (P < p1) {
+    const int img = P / n_w;
+    const int pstart = P;
+    const int pend = min(p1, (img + 1) * n_w);
+    float2 s[EPT], cc[EPT], scr[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) s[e] = cc[e] = make_float2(0.0f, 0.0f);
+    for (; P < pend; ++P) {
+      if ((P - pstart) % kAnchor == 0) {
+        // anchors: a rolled loop keeps the float-float screen evaluation of one output
+        // live at a time; the results pass through the free staging buffer (the one the
+        // next plane's tile goes to), before that copy is issued
+        float2 *s_anchor = stage_buf[(P + 1 - p0) & 1];
+#pragma unroll 1
+        for (int e = 0; e < EPT; ++e) {
+          const int kq = out_row(e / R1, e % R1);
+          const float sg = ((kq + kp) & 1) ? -1.0f : 1.0f;
+          float2 &st = s_step[e][threadIdx.x];
+          float2 a;
+          if constexpr (FP64S) {
+            if (P == pstart) screen_anchor<true, true>(sc, kp, kq, P, img, sg, a, st);
+            else screen_anchor<true, false>(sc, kp, kq, P, img, sg, a, st);
+          } else {
+            float2 &t2 = s_nm1[e][threadIdx.x];
+            if (P == pstart) {
+              bool valid;
+              const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+              t2 = valid ? make_float2(t.hi, t.lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
+              screen_from_t<true>(sc, t2, P, img, sg, a, st);
+            } else {
+              screen_from_t<false>(sc, t2, P, img, sg, a, st);
+            }
+          }
+          s_anchor[e * THREADS + threadIdx.x] = a;
+        }
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) scr[e] = s_anchor[e * THREADS + threadIdx.x];
+        __syncthreads();  // every read of the staging buffer done before the copy into it
+      }
+      if (P + 1 < p1)
+        stage_tile_async16<LA, THREADS>(stage_buf[(P + 1 - p0) & 1], planes + (size_t)(P + 1 - p0) * plane_elems, n,
+                                        LA * c, col0);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      float2 *tile = stage_buf[(P - p0) & 1];
+      float2 v[EPT];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = tile[(jt + r * TPL) * kCB + col];
+      dft<16, 1>(v);
+      __syncthreads();  // every stage-0 load of the tile done before the in-place exchange
+#pragma unroll
+      for (int r = 0; r < 16; ++r) tile[(16 * jt + r) * kCB + col] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < EPT / R1; ++b)
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[b * R1 + r] = tile[(jt + b * TPL + 16 * r) * kCB + col];
+#pragma unroll
+      for (int b = 0; b < EPT / R1; ++b) {
+#pragma unroll
+        for (int r = 1; r < R1; ++r) v[b * R1 + r] = cmul(v[b * R1 + r], s_tw1[b * (R1 - 1) + r - 1][jt]);
+        dft<R1, 1>(&v[b * R1]);
+      }
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float2 y = cmul(v[e], scr[e]);
+        if (kahan) kahan_add(s[e], cc[e], y);
+        else s[e] = cadd(s[e], y);
+        scr[e] = cmul(scr[e], s_step[e][threadIdx.x]);
+      }
+      __syncthreads();  // staging buffer reused by the next planes
+    }
+    const bool first_any = img * n_w >= p0;
+    const bool last_any = (img + 1) * n_w <= p1;
+    float2 *im = image + (size_t)img * n * n;
+    float2 *cp = comp ? comp + (size_t)img * n * n : nullptr;
+#pragma unroll
+    for (int b = 0; b < EPT / R1; ++b)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int e = b * R1 + r;
+        const int kq = out_row(b, r);
+        const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
+        flush_pixel(im, cp, (size_t)kq * n + kp, s[e], cc[e], first_any, last_any, flags, f);
       }
   }
 }
@@ -718,18 +979,18 @@ cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool p
 
 template <int LB, int DIR, bool TWF>
 static cudaError_t launch_cols_a(wst_plan_s *p, float2 *planes, int nplanes, const uint8_t *occ) {
-  if constexpr (LB >= 32) {  // persistent, staged, 32-column bands
-    constexpr int CB = 32;
-    auto kern = k_cols_a_pers<LB, DIR, TWF, CB>;
+  if constexpr (LB >= 32) {  // persistent, staged, 32-column bands, 16 elements per thread
+    constexpr int CB = 32, THREADS = LB / 16 * CB;
+    auto kern = k_cols_a16<LB, DIR, TWF>;
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ColCfg<LB, CB>::THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)nplanes * (p->n / LB) * (p->n / CB);
     long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
     if (grid > tiles) grid = tiles;
-    kern<<<(unsigned)grid, ColCfg<LB, CB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ, nplanes);
+    kern<<<(unsigned)grid, THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ, nplanes);
   } else {
     dim3 grd(p->n / kCB, p->n / LB, nplanes);
     k_cols_a<LB, DIR, TWF><<<grd, ColCfg<LB>::THREADS, 0, p->stream>>>(planes, tw_of(p), p->n, occ);
@@ -776,6 +1037,16 @@ template <int LA>
 static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                  float2 *comp, int flags) {
   dim3 grd(p->n / kCB, p->n / LA);
+  if constexpr (LA == 64 || LA == 128) {
+    constexpr int THREADS = LA / 16 * kCB;
+    if (fp64_screen(p))
+      k_cols_b16<LA, true><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
+                                                           image, comp, flags);
+    else
+      k_cols_b16<LA, false><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
+                                                            image, comp, flags);
+    return cudaGetLastError();
+  }
   if (fp64_screen(p))
     k_cols_b_acc<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
                                                                         screen_ctx(p), image, comp, flags);
