@@ -19,6 +19,19 @@
 //
 // Items are handed out by a device counter to persistent CTAs (one row or, for short
 // rows, RowCfg::RPC rows per CTA step).
+//
+// Fixed-point accumulation.  Shared-memory integer atomics sustain about three times
+// the rate of float ones on this GPU, and integer sums do not depend on the order of
+// the additions.  The sort leaves, per row bucket and bin of 64 columns, the sum of
+// max(|Re|, |Im|) of the weighted values whose taps reach the bin; for row q, M_b = the
+// sum of bin b over the buckets j0 = q - W + 1 ... q, and no cell of bin b can exceed
+// M_b G^2 (G the largest |kernel value|).  With B = max_b M_b G^2 and the quantum
+// delta = B / 2^30, each tap is rounded to a multiple of delta (error <= delta/2) and
+// every partial sum fits an int32 (|sum| <= 2^30 + c_q/2, c_q the visibility-rows of
+// the row).  For random-phase values the image error grows with B relative to the
+// typical value, so a row takes the fixed-point path only if its busiest bin holds at
+// most 2^13 times the row's mean magnitude (max_b M_b c_q <= 2^13 sum_b M_b); other
+// rows keep float atomics.
 #include "fft_core.cuh"
 
 namespace wst {
@@ -72,14 +85,28 @@ __device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q
   }
 }
 
+// one tap into the planar row: float atomics, or (FIXED) the value in units of the
+// row's quantum (qscale = 1/delta) as an integer atomic
+template <bool FIXED>
+__device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re, float im, float qscale) {
+  if constexpr (FIXED) {
+    atomicAdd(reinterpret_cast<int *>(sre) + c, __float2int_rn(re * qscale));
+    atomicAdd(reinterpret_cast<int *>(sim) + c, __float2int_rn(im * qscale));
+  } else {
+    atomicAdd(&sre[c], re);
+    atomicAdd(&sim[c], im);
+  }
+}
+
 // Accumulate the visibilities of rows j0 = q - d_lo ... q into the row, stored planar
 // (re[0..N), im[0..N)).  Their sub-buckets are contiguous in the sorted records, so the
 // range bnd[0] .. bnd[d_lo + 1] is split evenly over the row's threads, one visibility
 // per thread (two in flight); bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0
 // fixes the support at compile time.
-template <int N, int WT>
+template <int N, int WT, bool FIXED>
 __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *__restrict__ rec,
-                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt) {
+                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
+                                         float qscale) {
   constexpr int TPR = RowCfg<N>::TPR;
   const uint32_t s_end = bnd[d_lo + 1];
   if constexpr (WT > 0) {
@@ -101,10 +128,7 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
         const int i0 = rec_i0(r[h]);
         const float vre = r[h].vre * gy, vim = r[h].vim * gy;
 #pragma unroll
-        for (int a = 0; a < WT; ++a) {
-          atomicAdd(&sre[i0 + a], vre * g[a]);
-          atomicAdd(&sim[i0 + a], vim * g[a]);
-        }
+        for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale);
       }
     }
   } else {
@@ -118,8 +142,7 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
       const int i0 = rec_i0(r);
       for (int a = 0; a < W; ++a) {
         const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
-        atomicAdd(&sre[i0 + a], r.vre * g);
-        atomicAdd(&sim[i0 + a], r.vim * g);
+        add_tap<FIXED>(sre, sim, i0 + a, r.vre * g, r.vim * g, qscale);
       }
     }
   }
@@ -131,7 +154,8 @@ template <int N, bool FFT, int WT>
 __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const Record *__restrict__ rec,
                                              const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
                                              const KernelParams &kp, float2 *__restrict__ orow,
-                                             const float2 *twt, int jt) {
+                                             const float2 *twt, int jt, const float *__restrict__ binmag,
+                                             float g2, uint32_t *red) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -141,22 +165,68 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   const int W = WT > 0 ? WT : kp.support;
   float *sre = reinterpret_cast<float *>(srow), *sim = sre + N;  // planar accumulation
   const int d_lo = min(q, W - 1);
-  if (nonempty)
+  constexpr int NB = bins_per_row(N);
+  float bmax = 0.0f, btot = 0.0f;  // this thread's bins: largest and total magnitude sum
+  if (nonempty) {
     for (int i = jt; i <= d_lo + 1; i += TPR) bnd[i] = off[(b0 + q - d_lo + i) * kColBlocks];
+    for (int b = jt; b < NB; b += TPR) {
+      float m = 0.0f;
+      for (int d = 0; d <= d_lo; ++d) m += __ldg(binmag + (size_t)(b0 + q - d) * NB + b);
+      bmax = fmaxf(bmax, m);
+      btot += m;
+    }
+  }
+  if (jt == 0) red[0] = red[1] = 0u;
   zero_row<N>(srow, jt);
   __syncthreads();
-  if (nonempty) grid_row<N, WT>(sre, sim, rec, bnd, d_lo, kp, jt);
+  if (nonempty) {  // row maximum and total (non-negative floats order like their bits)
+    if constexpr (TPR >= 32) {
+      for (int o = 16; o > 0; o >>= 1) btot += __shfl_xor_sync(0xFFFFFFFFu, btot, o);
+      const uint32_t mb = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bmax));
+      if ((jt & 31) == 0) {
+        atomicMax(&red[0], mb);
+        atomicAdd(reinterpret_cast<float *>(&red[1]), btot);
+      }
+    } else {
+      atomicMax(&red[0], __float_as_uint(bmax));
+      atomicAdd(reinterpret_cast<float *>(&red[1]), btot);
+    }
+  }
   __syncthreads();
+  // the same decision and quantum in every thread of the row
+  const uint32_t cnt = nonempty ? bnd[d_lo + 1] - bnd[0] : 0u;
+  const float mmax = __uint_as_float(red[0]), mtot = __uint_as_float(red[1]);
+  const float bound = mmax * g2;
+  const bool fixed = nonempty && cnt < (1u << 30) && bound >= 0x1p-90f && bound <= 0x1p+100f &&
+                     mmax * (float)cnt <= 0x1p13f * mtot;
+  const float delta = fixed ? bound * 0x1p-30f : 1.0f;
+  if (nonempty) {
+    if (fixed) grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 0x1p30f / bound);
+    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f);
+  }
+  __syncthreads();
+  const int *ire = reinterpret_cast<const int *>(sre), *iim = reinterpret_cast<const int *>(sim);
   if constexpr (FFT) {
     float2 v[EPT];
+    if (fixed) {
 #pragma unroll
-    for (int b = 0; b < EPT / R0; ++b)
+      for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
-      for (int r = 0; r < R0; ++r) {
-        const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
-        const float sg = ((idx + q) & 1) ? -1.0f : 1.0f;  // centring sign
-        v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
-      }
+        for (int r = 0; r < R0; ++r) {
+          const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+          const float sg = ((idx + q) & 1) ? -delta : delta;  // centring sign and quantum
+          v[b * R0 + r] = make_float2(sg * __int2float_rn(ire[idx]), sg * __int2float_rn(iim[idx]));
+        }
+    } else {
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int idx = in_index<N, EPT, TPR, 0>(jt, b, r);
+          const float sg = ((idx + q) & 1) ? -1.0f : 1.0f;  // centring sign
+          v[b * R0 + r] = make_float2(sg * sre[idx], sg * sim[idx]);
+        }
+    }
     __syncthreads();  // natural-order reads done before the padded writes
     const TableTw<N, EPT, TPR, 1> twp{twt, jt};
     stage_compute_f<N, EPT, TPR, 0, 1>(v, jt, twp);
@@ -170,8 +240,13 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
           __stcs(&orow[out_index<N, EPT, TPR, NST - 1>(jt, b, r)], v[b * RL + r]);
     }
   } else {
-    if (orow)
-      for (int i = jt; i < N; i += TPR) orow[i] = make_float2(sre[i], sim[i]);
+    if (orow) {
+      if (fixed)
+        for (int i = jt; i < N; i += TPR)
+          orow[i] = make_float2(delta * __int2float_rn(ire[i]), delta * __int2float_rn(iim[i]));
+      else
+        for (int i = jt; i < N; i += TPR) orow[i] = make_float2(sre[i], sim[i]);
+    }
   }
   __syncthreads();  // the row buffer is reused by the next row
 }
@@ -182,16 +257,32 @@ template <int N, bool FFT, int WT>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
 k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int np,
             KernelParams kp, float2 *__restrict__ out, uint8_t *__restrict__ occ,
-            unsigned long long *__restrict__ counter, Tw tw) {
+            unsigned long long *__restrict__ counter, Tw tw, const float *__restrict__ binmag) {
   using C = RowCfg<N>;
   constexpr int TPR = C::TPR, RPC = C::RPC;
   extern __shared__ __align__(16) float2 sm_rows[];
   __shared__ long long s_item;
   __shared__ uint32_t s_bnd[RPC][kMaxSupport + 2];
+  __shared__ uint32_t s_gmax;  // largest |kernel value| (FP32 bits)
+  __shared__ uint32_t s_red[RPC][2];  // per row: largest bin magnitude (bits), total (float)
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
   float2 *twt = sm_rows + RPC * C::PADL;  // twiddle tables (visible after the first barrier)
   if constexpr (FFT) fill_line_tables<N, C::EPT, TPR>(twt, tw);
+  // G^2 of the fixed-point bound (G = 1 for the Gaussian and the ES kernel, the largest
+  // |sample| of a table: linear interpolation stays below it)
+  if (threadIdx.x == 0) s_gmax = __float_as_uint(1.0f);
+  if (kp.kind == WST_KERNEL_TABLE) {
+    __syncthreads();
+    float gm = 0.0f;
+    for (int i = threadIdx.x; i < kp.table_len; i += blockDim.x) gm = fmaxf(gm, fabsf(__ldg(kp.table + i)));
+    if (threadIdx.x == 0) s_gmax = 0u;
+    __syncthreads();
+    atomicMax(&s_gmax, __float_as_uint(gm));
+  }
+  __syncthreads();
+  const float gmax = __uint_as_float(s_gmax);
+  const float g2 = gmax * gmax;
   const long long total = (long long)np * N;
   const int W = WT > 0 ? WT : kp.support;
   auto row_empty = [&](long long item) {
@@ -232,7 +323,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const long long item = base + (e >> 1);
         const int pl = (int)(item / N), q = (int)(item % N);
         grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
-                                 out + ((int64_t)pl * N + q) * N, twt, jt);
+                                 out + ((int64_t)pl * N + q) * N, twt, jt, binmag, g2, s_red[0]);
       }
     }
   } else {
@@ -249,7 +340,8 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       const bool empty = !valid || row_empty(item);
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
-      grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt);
+      grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt,
+                               binmag, g2, s_red[rl]);
     }
   }
 }
@@ -417,7 +509,7 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
   kern<<<grid, C::THREADS, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, np, kernel_params(p), out,
-                                             p->W_.occ, counter, tw_half(p));
+                                             p->W_.occ, counter, tw_half(p), p->W_.binmag);
   return cudaGetLastError();
 }
 

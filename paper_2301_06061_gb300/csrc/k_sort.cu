@@ -313,11 +313,13 @@ static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cuda
 // bucket's cursor, advanced by a warp-aggregated atomic (one per distinct key in the
 // warp); kScatterIlp visibilities are in flight per thread, their loads and atomics
 // issued before any result is used.  The order inside a bucket is not specified.
+// For the gridder's fixed-point bound, max(|Re|, |Im|) of each weighted value is added to
+// the column bins its W taps reach (one or two) of its row bucket.
 constexpr int kScatterIlp = 4;
 
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
                           const uint4 *__restrict__ keyinfo, uint32_t *__restrict__ cursor, int64_t n_vis,
-                          Record *__restrict__ records) {
+                          Record *__restrict__ records, float *__restrict__ binmag, int nb, int W) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   // uniform trip count across the warp (warp-level votes below)
@@ -354,7 +356,14 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
       if (!kept) continue;
       const uint32_t pos = b + __popc(peers[h] & ((1u << lane) - 1u));
       uint4 *dst = reinterpret_cast<uint4 *>(records + pos);
-      dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(val[h].x * wt[h]), __float_as_uint(val[h].y * wt[h]));
+      const float vre = val[h].x * wt[h], vim = val[h].y * wt[h];
+      const float mag = fmaxf(fabsf(vre), fabsf(vim));
+      const int i0 = (int)(ki[h].z >> 18);
+      const int bl = min(i0 >> kBinShift, nb - 1), bh = min((i0 + W - 1) >> kBinShift, nb - 1);
+      float *bins = binmag + (size_t)(ki[h].x / kColBlocks) * nb;
+      atomicAdd(bins + bl, mag);
+      if (bh != bl) atomicAdd(bins + bh, mag);
+      dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(vre), __float_as_uint(vim));
       dst[1] = make_uint4((uint32_t)(w0 + h * stride + lane), __float_as_uint(wt[h]), 0u, 0u);
     }
   }
@@ -404,8 +413,10 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   if ((e = cudaGetLastError())) return e;
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
   if ((e = cudaMemcpyAsync(ws.cursor, ws.offsets, sizeof(uint32_t) * nb1, cudaMemcpyDeviceToDevice, s))) return e;
+  const int nb = bins_per_row(p->n);
+  if ((e = cudaMemsetAsync(ws.binmag, 0, sizeof(float) * (size_t)(p->n_buckets / kColBlocks) * nb, s))) return e;
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(vis, weight, ws.keyinfo, ws.cursor, p->n_vis,
-                                                              ws.records);
+                                                              ws.records, ws.binmag, nb, p->W);
   p->launches += 1;
   return cudaGetLastError();
 }

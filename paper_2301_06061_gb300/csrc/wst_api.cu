@@ -43,7 +43,7 @@ int ilog2(int x) {
 }
 
 struct Layout {
-  size_t keyinfo_planes, records, offsets, cursor, scan_tmp, counters, wminmax, occ, comp, total;
+  size_t keyinfo_planes, records, offsets, cursor, scan_tmp, counters, wminmax, occ, binmag, comp, total;
 };
 
 Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
@@ -67,6 +67,8 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   off += align_up((size_t)2 * p->batch * sizeof(uint32_t));
   L.occ = off;
   off += align_up((size_t)p->n_planes * p->n);
+  L.binmag = off;
+  off += align_up((size_t)(p->n_buckets / kColBlocks) * bins_per_row(p->n) * sizeof(float));
   L.comp = off;
   if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n * p->n * sizeof(float2));
   L.total = off;
@@ -285,6 +287,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.counters = (unsigned long long *)(p->ws + L.counters);
   W.wminmax = (uint32_t *)(p->ws + L.wminmax);
   W.occ = (uint8_t *)(p->ws + L.occ);
+  W.binmag = (float *)(p->ws + L.binmag);
   W.comp = (p->chunk < p->n_planes) ? (float2 *)(p->ws + L.comp) : nullptr;
   W.bytes = L.total;
   p->launches = 0;

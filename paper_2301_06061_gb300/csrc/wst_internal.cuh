@@ -16,6 +16,11 @@ constexpr int kColBlocks = 1;    // sub-buckets per row (by tap-start column; a 
                                  // are contiguous).  More than one spreads the histogram atomics
                                  // but enlarges the offsets table and the scan: slower at 16384^2.
 constexpr uint32_t kDropKey = 0xFFFFFFFFu;
+// Column bins of the fixed-point gridder's bound: for every row bucket (image, plane, j0)
+// the sort sums max(|Re|, |Im|) of the weighted values whose W taps reach each bin of
+// kBinCols columns.
+constexpr int kBinCols = 64, kBinShift = 6;
+__host__ __device__ constexpr int bins_per_row(int n) { return n >= kBinCols ? n / kBinCols : 1; }
 
 // counters[] slots in the workspace
 enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_WORK = 4, CNT_SLOTS = 8 };
@@ -79,6 +84,7 @@ struct Workspace {
   unsigned long long *counters;  // CNT_* slots
   uint32_t *wminmax;   // per image: ordered-int min and max of finite w
   uint8_t *occ;        // per (plane of the chunk, row): 1 if any visibility reaches the row
+  float *binmag;       // per (row bucket, column bin): magnitude sum (fixed-point bound)
   float2 *planes;      // chunk of planes
   float2 *comp;        // Kahan compensation image [batch][N*N]
   size_t bytes;
