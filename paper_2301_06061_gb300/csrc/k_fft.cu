@@ -252,111 +252,18 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Persistent form of pass CA for the long columns: each CTA walks tiles (plane, a,
-// CB-column band; 32 columns = 256-byte row segments) in band-fastest order; the next tile's rows are copied into a
-// shared staging buffer (cp.async; rows the gridder left empty are zero-filled instead
-// of read) while the current one is transformed, and the stage twiddles, identical for
-// every tile, stay in registers.
-template <int LB, int DIR, bool TW_FIRST, int CB>
-__global__ void __launch_bounds__(ColCfg<LB, CB>::THREADS, 1024 / ColCfg<LB, CB>::THREADS)
-k_cols_a_pers(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
-  using C = ColCfg<LB, CB>;
-  constexpr int EPT = C::EPT, TPL = C::TPL;
-  constexpr int NST = num_stages(LB, EPT);
-  constexpr int R0 = stage_radix(LB, EPT, 0);
-  constexpr int RL = stage_radix(LB, EPT, NST - 1);
-  constexpr int PIECES = LB * (CB / 2);  // 16-byte pieces per tile
-  __shared__ float2 sm[LB * C::PADW];
-  __shared__ __align__(16) float2 stage[2][LB * CB];
-  const int A = n / LB;
-  // tile t -> band = t mod bands, a = (t / bands) mod A, plane z = t / (bands A); all
-  // powers of two, so shifts and masks (no integer division in the loop)
-  const int lg_bands = 31 - __clz(n / CB), lg_A = 31 - __clz(A);
-  const int total = nplanes << (lg_bands + lg_A);
-  const int col = threadIdx.x % CB, jt = threadIdx.x / CB;
-  auto smi = [col](int i) { return i * C::PADW + col; };
-  float2 twr[total_tw_count<LB, EPT>() > 0 ? total_tw_count<LB, EPT>() : 1];
-  all_twiddles<LB, EPT, TPL, DIR>(twr, jt, tw, A);
-  const size_t rstride = (size_t)A * n;  // line element i -> row a + A*i
-  constexpr int PPT = PIECES / C::THREADS;  // pieces per thread (4)
-  static_assert(PIECES % C::THREADS == 0, "pieces");
-  // occupancy of the rows of this thread's pieces, loaded one tile ahead of their use
-  auto load_flags = [&](int t, bool (&f)[PPT]) {
-    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int i = (threadIdx.x + k * C::THREADS) / (CB / 2);
-      f[k] = t >= total || !occ || occ[(size_t)z * n + a + A * i];
-    }
-  };
-  auto issue = [&](int t, float2 *buf, const bool (&f)[PPT]) {
-    const int band = t & ((1 << lg_bands) - 1);
-    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
-    const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * CB;
-    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      const int c = threadIdx.x + k * C::THREADS;
-      const int i = c / (CB / 2), part = c % (CB / 2);
-      if (f[k])
-        cp_async16(sbuf + (uint32_t)(i * CB + 2 * part) * 8u, src + i * rstride + 2 * part);
-      else
-        reinterpret_cast<float4 *>(buf)[(i * CB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-  };
-  int t = blockIdx.x;
-  bool f0[PPT], f1[PPT];
-  load_flags(t, f0);
-  load_flags(t + gridDim.x, f1);
-  if (t < total) issue(t, stage[0], f0);
-  cp_async_commit();
-  for (int it = 0; t < total; ++it, t += gridDim.x) {
-    if (t + gridDim.x < total) issue(t + gridDim.x, stage[(it + 1) & 1], f1);
-    cp_async_commit();
-    load_flags(t + 2 * (int)gridDim.x, f1);  // consumed by the next iteration's copies
-    cp_async_wait<1>();
-    __syncthreads();
-    const int band = t & ((1 << lg_bands) - 1);
-    const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
-    const float2 *buf = stage[it & 1];
-    float2 v[EPT];
-#pragma unroll
-    for (int b = 0; b < EPT / R0; ++b)
-#pragma unroll
-      for (int rr = 0; rr < R0; ++rr) {
-        const int i = in_index<LB, EPT, TPL, 0>(jt, b, rr);
-        float2 x = buf[i * CB + col];
-        if (TW_FIRST) x = cmul(x, twiddle(tw, a * i, DIR));
-        v[b * R0 + rr] = x;
-      }
-    stage_compute_pre<LB, EPT, 0, DIR>(v, twr);
-    if constexpr (NST > 1) {
-      middle_stages_pre<LB, EPT, TPL, 1, DIR>(v, jt, sm, smi, twr);
-      stage_compute_pre<LB, EPT, NST - 1, DIR>(v, twr);
-    }
-    float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * CB + col;
-#pragma unroll
-    for (int b = 0; b < EPT / RL; ++b)
-#pragma unroll
-      for (int rr = 0; rr < RL; ++rr) {
-        const int c = out_index<LB, EPT, TPL, NST - 1>(jt, b, rr);
-        float2 x = v[b * RL + rr];
-        if (!TW_FIRST) x = cmul(x, twiddle(tw, a * c, DIR));
-        __stcs(&dst[(size_t)c * rstride], x);
-      }
-    __syncthreads();  // staging buffer and shared memory reused
-  }
-  cp_async_wait<0>();
-}
-
-// Pass CA with 16 elements per thread (LB = 32, 64, 128: radix 16 then LB/16), for the
-// same persistent tile walk: one exchange between the two register stages, made in
-// place in the tile's own staging buffer (a warp covers 32 columns at one line
-// position, so shared-memory accesses are conflict-free without padding and twiddles
-// are warp-uniform), and the factors w_N^{a c} of the tile taken from a shared table
-// filled at the top of each tile.
+// Pass CA, persistent: each CTA walks tiles (plane, a, 32-column band: 256-byte row
+// segments) in band-fastest order; the next tile's rows are copied into a shared staging
+// buffer with cp.async while the current one is transformed (rows the gridder left
+// empty are zero-filled instead of read, their flags loaded a tile ahead).  16 elements
+// per thread (LB = 32, 64, 128: radix 16, then LB/16 with the stage twiddles in
+// registers); one exchange between the two register stages through a buffer of its
+// own, so a tile costs two barriers.  A warp covers 32 columns at one line position:
+// shared-memory accesses are conflict-free without padding and twiddles are
+// warp-uniform.  The factors w_N^{a c} of a tile come from a shared table filled one
+// tile ahead (three in rotation).
 template <int LB, int DIR, bool TW_FIRST>
-__global__ void __launch_bounds__(LB / 16 * 32, 768 / (LB / 16 * 32))
+__global__ void __launch_bounds__(LB / 16 * 32, 512 / (LB / 16 * 32))
 k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
   constexpr int CB = 32, EPT = 16, TPL = LB / EPT, THREADS = TPL * CB;
   constexpr int R1 = LB / 16;  // radix of the second stage
@@ -365,7 +272,8 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
   constexpr int PPT = PIECES / THREADS;     // pieces per thread (8)
   static_assert(PIECES % THREADS == 0, "pieces");
   __shared__ __align__(16) float2 stage[2][LB * CB];
-  __shared__ float2 s_tw[LB];  // w_N^{DIR a c}, c < LB, for the tile being transformed
+  __shared__ float2 xbuf[LB * CB];  // exchange between the two register stages
+  __shared__ float2 s_tw[3][LB];    // w_N^{DIR a c}, c < LB, of the tiles in flight
   const int A = n / LB;
   const int lg_bands = 31 - __clz(n / CB), lg_A = 31 - __clz(A);
   const int total = nplanes << (lg_bands + lg_A);
@@ -396,39 +304,48 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
         reinterpret_cast<float4 *>(buf)[(i * CB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   };
+  auto fill_tw = [&](int t, float2 *dst) {
+    const int a = (t >> lg_bands) & (A - 1);
+    if (threadIdx.x < LB) dst[threadIdx.x] = twiddle(tw, (a * (int)threadIdx.x) & (n - 1), DIR);
+  };
   int t = blockIdx.x;
   bool f0[PPT], f1[PPT];
   load_flags(t, f0);
   load_flags(t + gridDim.x, f1);
-  if (t < total) issue(t, stage[0], f0);
+  if (t < total) {
+    issue(t, stage[0], f0);
+    fill_tw(t, s_tw[0]);
+  }
   cp_async_commit();
   for (int it = 0; t < total; ++it, t += gridDim.x) {
-    if (t + gridDim.x < total) issue(t + gridDim.x, stage[(it + 1) & 1], f1);
+    if (t + gridDim.x < total) {
+      issue(t + gridDim.x, stage[(it + 1) & 1], f1);
+      fill_tw(t + gridDim.x, s_tw[(it + 1) % 3]);
+    }
     cp_async_commit();
     load_flags(t + 2 * (int)gridDim.x, f1);
     const int band = t & ((1 << lg_bands) - 1);
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
-    if (threadIdx.x < LB) s_tw[threadIdx.x] = twiddle(tw, (a * (int)threadIdx.x) & (n - 1), DIR);
+    const float2 *tws = s_tw[it % 3];
     cp_async_wait<1>();
-    __syncthreads();
-    float2 *buf = stage[it & 1];
+    __syncthreads();  // tile it landed; the exchange buffer's readers of tile it-1 are done
+    const float2 *buf = stage[it & 1];
     float2 v[EPT];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int i = jt + r * TPL;
       float2 x = buf[i * CB + col];
-      if (TW_FIRST) x = cmul(x, s_tw[i]);
+      if (TW_FIRST) x = cmul(x, tws[i]);
       v[r] = x;
     }
     dft<16, DIR>(v);
-    __syncthreads();  // every stage-0 load of the tile done before the in-place exchange
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf[(16 * jt + r) * CB + col] = v[r];
-    __syncthreads();
+    for (int r = 0; r < 16; ++r) xbuf[(16 * jt + r) * CB + col] = v[r];
+    __syncthreads();  // exchange complete; every read of the staging buffer is done
 #pragma unroll
     for (int b = 0; b < 16 / R1; ++b)
 #pragma unroll
-      for (int r = 0; r < R1; ++r) v[b * R1 + r] = buf[(jt + b * TPL + 16 * r) * CB + col];
+      for (int r = 0; r < R1; ++r) v[b * R1 + r] = xbuf[(jt + b * TPL + 16 * r) * CB + col];
     stage_compute_pre<LB, EPT, 1, DIR>(v, twr);
     float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * CB + col;
 #pragma unroll
@@ -437,10 +354,9 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
       for (int r = 0; r < R1; ++r) {
         const int c = jt + b * TPL + 16 * r;
         float2 x = v[b * R1 + r];
-        if (!TW_FIRST) x = cmul(x, s_tw[c]);
+        if (!TW_FIRST) x = cmul(x, tws[c]);
         __stcs(&dst[(size_t)c * rstride], x);
       }
-    __syncthreads();  // staging buffer and twiddle table reused
   }
   cp_async_wait<0>();
 }

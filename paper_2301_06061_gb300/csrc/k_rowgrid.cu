@@ -28,10 +28,14 @@
 // M_b G^2 (G the largest |kernel value|).  With B = max_b M_b G^2 and the quantum
 // delta = B / 2^30, each tap is rounded to a multiple of delta (error <= delta/2) and
 // every partial sum fits an int32 (|sum| <= 2^30 + c_q/2, c_q the visibility-rows of
-// the row).  For random-phase values the image error grows with B relative to the
-// typical value, so a row takes the fixed-point path only if its busiest bin holds at
-// most 2^13 times the row's mean magnitude (max_b M_b c_q <= 2^13 sum_b M_b); other
-// rows keep float atomics.
+// the row).  The bound is a sum of magnitudes, while a cell of random-phase values grows
+// like the square root of their number, so the rounding error relative to the cells
+// grows with the occupancy of the busiest bin: a row takes the fixed-point path only if
+// max_b M_b is at most kFixedBinCap times its mean magnitude per visibility-row (the
+// bins count a visibility-row once per bin it reaches, 1 + (W - 1)/64 bins on
+// average); other rows keep float atomics.  On the benchmark workload about half of the
+// taps take the fixed-point path, and the image error against the FP64 oracle stays at
+// the level of the all-float path.
 #include "fft_core.cuh"
 
 namespace wst {
@@ -84,6 +88,8 @@ __device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q
     for (int a = 0; a < WT; ++a) g[a] = kernel_eval(kp, (float)a - kp.half + gx);
   }
 }
+
+constexpr int kFixedBinCap = 512;
 
 // one tap into the planar row: float atomics, or (FIXED) the value in units of the
 // row's quantum (qscale = 1/delta) as an integer atomic
@@ -198,7 +204,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   const float mmax = __uint_as_float(red[0]), mtot = __uint_as_float(red[1]);
   const float bound = mmax * g2;
   const bool fixed = nonempty && cnt < (1u << 30) && bound >= 0x1p-90f && bound <= 0x1p+100f &&
-                     mmax * (float)cnt <= 0x1p13f * mtot;
+                     mmax * (float)cnt * (1.0f + (float)(W - 1) / (float)kBinCols) <= (float)kFixedBinCap * mtot;
   const float delta = fixed ? bound * 0x1p-30f : 1.0f;
   if (nonempty) {
     if (fixed) grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 0x1p30f / bound);

@@ -211,10 +211,10 @@ def test_grid_fixed_point_rows_are_deterministic(wst):
 
 
 def test_grid_and_image_dense_rows_keep_float_atomics(wst):
-    """A row whose busiest 64-column bin holds more than 2^13 times the row's mean
-    magnitude keeps float atomics (here 1.1M visibility-rows over four bins); a plane
-    holding such rows and ordinary (fixed-point) ones matches the oracle, gridded and
-    imaged."""
+    """A row whose busiest 64-column bin holds more than 512 times the row's mean
+    magnitude per visibility-row keeps float atomics (here 1.1M visibility-rows over four
+    bins); a plane holding such rows and ordinary (fixed-point) ones matches the oracle,
+    gridded and imaged."""
     rng = np.random.default_rng(5)
     n, fov, nd, ns = 256, 0.1, 1_100_000, 4000
     u = np.concatenate([rng.uniform(-1200.0, 1200.0, nd), rng.uniform(-1200.0, 1200.0, ns)]).astype(np.float32)
