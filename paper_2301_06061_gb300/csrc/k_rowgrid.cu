@@ -21,21 +21,25 @@
 // rows, RowCfg::RPC rows per CTA step).
 //
 // Fixed-point accumulation.  Shared-memory integer atomics sustain about three times
-// the rate of float ones on this GPU, and integer sums do not depend on the order of
-// the additions.  The sort leaves, per row bucket and bin of 64 columns, the sum of
-// max(|Re|, |Im|) of the weighted values whose taps reach the bin; for row q, M_b = the
-// sum of bin b over the buckets j0 = q - W + 1 ... q, and no cell of bin b can exceed
-// M_b G^2 (G the largest |kernel value|).  With B = max_b M_b G^2 and the quantum
-// delta = B / 2^30, each tap is rounded to a multiple of delta (error <= delta/2) and
-// every partial sum fits an int32 (|sum| <= 2^30 + c_q/2, c_q the visibility-rows of
-// the row).  The bound is a sum of magnitudes, while a cell of random-phase values grows
-// like the square root of their number, so the rounding error relative to the cells
-// grows with the occupancy of the busiest bin: a row takes the fixed-point path only if
-// max_b M_b is at most kFixedBinCap times its mean magnitude per visibility-row (the
-// bins count a visibility-row once per bin it reaches, 1 + (W - 1)/64 bins on
-// average); other rows keep float atomics.  On the benchmark workload about half of the
-// taps take the fixed-point path, and the image error against the FP64 oracle stays at
-// the level of the all-float path.
+// the rate of float ones on this GPU.  The sort leaves, per row bucket and bin of 64
+// columns, the sum of max(|Re|, |Im|) of the weighted values whose taps reach the bin;
+// for row q, M_b = the sum of bin b over the buckets j0 = q - W + 1 ... q bounds every
+// cell of bin b by M_b G^2 (G the largest |kernel value|).  With B = max_b M_b G^2 the
+// row is accumulated in int32 units of delta = B / 2^34: each tap is rounded to a
+// multiple of delta (error <= delta/2).  B is a sum of magnitudes, far above the cells
+// of a dense bin (random phases add up like a square root), which is what makes the
+// fine quantum usable; but a cell or a single tap can exceed 2^31 delta = B/8 (a
+// dominant visibility, a coherent pile-up), so every integer atomic returns the old
+// value and the kernel checks for a wrapped partial sum or a saturated conversion: if
+// any occurred in the row, the row is zeroed and accumulated again with float atomics.
+// Rows whose busiest bin holds fewer than 64 mean contributions take delta = B / 2^30,
+// which cannot overflow (sparse rows would otherwise overflow often; their cells are
+// few-term sums, for which the coarser quantum is precise enough).
+// Rows whose busiest bin holds more than kFixedBinCap times the row's mean magnitude
+// per visibility-row (the bins count a visibility-row once per bin it reaches,
+// 1 + (W - 1)/64 bins on average) go straight to float atomics.  On the benchmark
+// workload the image error against the FP64 oracle equals that of all-float
+// accumulation.  Images narrower than kFixedMinN (8192) keep float atomics throughout.
 #include "fft_core.cuh"
 
 namespace wst {
@@ -89,15 +93,25 @@ __device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q
   }
 }
 
-constexpr int kFixedBinCap = 512;
+constexpr int kFixedBinCap = 8192;
+// Short rows (N < kFixedMinN) carry few visibility-rows each: the bound's extra barriers
+// cost more than the float atomics they would save, so they keep float accumulation.
+template <int N>
+constexpr bool kFixedRows = N >= kFixedMinN;
 
 // one tap into the planar row: float atomics, or (FIXED) the value in units of the
-// row's quantum (qscale = 1/delta) as an integer atomic
+// row's quantum (qscale = 1/delta) as an integer atomic; ovf turns negative if the
+// conversion saturated or the cell's partial sum wrapped around
 template <bool FIXED>
-__device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re, float im, float qscale) {
+__device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re, float im, float qscale, int &ovf) {
   if constexpr (FIXED) {
-    atomicAdd(reinterpret_cast<int *>(sre) + c, __float2int_rn(re * qscale));
-    atomicAdd(reinterpret_cast<int *>(sim) + c, __float2int_rn(im * qscale));
+    const float fr = re * qscale, fi = im * qscale;
+    const int xr = __float2int_rn(fr), xi = __float2int_rn(fi);
+    const int o1 = atomicAdd(reinterpret_cast<int *>(sre) + c, xr);
+    const int o2 = atomicAdd(reinterpret_cast<int *>(sim) + c, xi);
+    // a tap outside the int32 range (saturated conversion) or a partial sum that wrapped
+    ovf |= ((o1 ^ (o1 + xr)) & (xr ^ (o1 + xr))) | ((o2 ^ (o2 + xi)) & (xi ^ (o2 + xi))) |
+           (fmaxf(fabsf(fr), fabsf(fi)) >= 0x1p31f ? -1 : 0);
   } else {
     atomicAdd(&sre[c], re);
     atomicAdd(&sim[c], im);
@@ -110,10 +124,11 @@ __device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re,
 // per thread (two in flight); bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0
 // fixes the support at compile time.
 template <int N, int WT, bool FIXED>
-__device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *__restrict__ rec,
-                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
-                                         float qscale) {
+__device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__restrict__ rec,
+                                        const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
+                                        float qscale) {
   constexpr int TPR = RowCfg<N>::TPR;
+  int ovf = 0;
   const uint32_t s_end = bnd[d_lo + 1];
   if constexpr (WT > 0) {
     const float q = expf(-2.0f * kp.inv2s2);
@@ -134,7 +149,7 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
         const int i0 = rec_i0(r[h]);
         const float vre = r[h].vre * gy, vim = r[h].vim * gy;
 #pragma unroll
-        for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale);
+        for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale, ovf);
       }
     }
   } else {
@@ -148,10 +163,11 @@ __device__ __forceinline__ void grid_row(float *sre, float *sim, const Record *_
       const int i0 = rec_i0(r);
       for (int a = 0; a < W; ++a) {
         const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
-        add_tap<FIXED>(sre, sim, i0 + a, r.vre * g, r.vim * g, qscale);
+        add_tap<FIXED>(sre, sim, i0 + a, r.vre * g, r.vim * g, qscale, ovf);
       }
     }
   }
+  return ovf;
 }
 
 // One non-empty row q of a plane: accumulate, transform (FFT) and write it.  Every
@@ -175,7 +191,8 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   float bmax = 0.0f, btot = 0.0f;  // this thread's bins: largest and total magnitude sum
   if (nonempty) {
     for (int i = jt; i <= d_lo + 1; i += TPR) bnd[i] = off[(b0 + q - d_lo + i) * kColBlocks];
-    for (int b = jt; b < NB; b += TPR) {
+    if constexpr (kFixedRows<N>)
+      for (int b = jt; b < NB; b += TPR) {
       float m = 0.0f;
       for (int d = 0; d <= d_lo; ++d) m += __ldg(binmag + (size_t)(b0 + q - d) * NB + b);
       bmax = fmaxf(bmax, m);
@@ -185,7 +202,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   if (jt == 0) red[0] = red[1] = 0u;
   zero_row<N>(srow, jt);
   __syncthreads();
-  if (nonempty) {  // row maximum and total (non-negative floats order like their bits)
+  if (kFixedRows<N> && nonempty) {  // row maximum and total (non-negative floats order like their bits)
     if constexpr (TPR >= 32) {
       for (int o = 16; o > 0; o >>= 1) btot += __shfl_xor_sync(0xFFFFFFFFu, btot, o);
       const uint32_t mb = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bmax));
@@ -198,23 +215,39 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
       atomicAdd(reinterpret_cast<float *>(&red[1]), btot);
     }
   }
-  __syncthreads();
+  if constexpr (kFixedRows<N>) __syncthreads();
   // the same decision and quantum in every thread of the row
   const uint32_t cnt = nonempty ? bnd[d_lo + 1] - bnd[0] : 0u;
   const float mmax = __uint_as_float(red[0]), mtot = __uint_as_float(red[1]);
   const float bound = mmax * g2;
-  const bool fixed = nonempty && cnt < (1u << 30) && bound >= 0x1p-90f && bound <= 0x1p+100f &&
-                     mmax * (float)cnt * (1.0f + (float)(W - 1) / (float)kBinCols) <= (float)kFixedBinCap * mtot;
-  const float delta = fixed ? bound * 0x1p-30f : 1.0f;
+  // n_eff: the busiest bin's magnitude in units of the row's mean per visibility-row
+  const float n_eff = mmax * (float)cnt * (1.0f + (float)(W - 1) / (float)kBinCols) / fmaxf(mtot, 0x1p-126f);
+  const bool fixed = kFixedRows<N> && nonempty && cnt < (1u << 30) && bound >= 0x1p-90f && bound <= 0x1p+100f &&
+                     n_eff <= (float)kFixedBinCap;
+  // a bin of fewer than ~64 mean contributions may hold a single tap above B/8: such rows
+  // take delta = B / 2^30, with which no tap or partial sum can leave the int32 range
+  const float unit = n_eff >= 64.0f ? 0x1p-34f : 0x1p-30f;
+  bool fx = fixed;
+  int ovf = 0;
   if (nonempty) {
-    if (fixed) grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 0x1p30f / bound);
+    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit));
     else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f);
   }
-  __syncthreads();
+  bool redo = false;  // a tap or a partial sum left the int32 range: accumulate in float
+  if constexpr (kFixedRows<N>) redo = __syncthreads_or(ovf < 0);
+  else __syncthreads();
+  if (redo) {
+    zero_row<N>(srow, jt);
+    __syncthreads();
+    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f);
+    fx = false;
+    __syncthreads();
+  }
+  const float delta = fx ? bound * unit : 1.0f;
   const int *ire = reinterpret_cast<const int *>(sre), *iim = reinterpret_cast<const int *>(sim);
   if constexpr (FFT) {
     float2 v[EPT];
-    if (fixed) {
+    if (fx) {
 #pragma unroll
       for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
@@ -247,7 +280,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
     }
   } else {
     if (orow) {
-      if (fixed)
+      if (fx)
         for (int i = jt; i < N; i += TPR)
           orow[i] = make_float2(delta * __int2float_rn(ire[i]), delta * __int2float_rn(iim[i]));
       else

@@ -358,11 +358,13 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
       uint4 *dst = reinterpret_cast<uint4 *>(records + pos);
       const float vre = val[h].x * wt[h], vim = val[h].y * wt[h];
       const float mag = fmaxf(fabsf(vre), fabsf(vim));
-      const int i0 = (int)(ki[h].z >> 18);
-      const int bl = min(i0 >> kBinShift, nb - 1), bh = min((i0 + W - 1) >> kBinShift, nb - 1);
-      float *bins = binmag + (size_t)(ki[h].x / kColBlocks) * nb;
-      atomicAdd(bins + bl, mag);
-      if (bh != bl) atomicAdd(bins + bh, mag);
+      if (binmag) {
+        const int i0 = (int)(ki[h].z >> 18);
+        const int bl = min(i0 >> kBinShift, nb - 1), bh = min((i0 + W - 1) >> kBinShift, nb - 1);
+        float *bins = binmag + (size_t)(ki[h].x / kColBlocks) * nb;
+        atomicAdd(bins + bl, mag);
+        if (bh != bl) atomicAdd(bins + bh, mag);
+      }
       dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(vre), __float_as_uint(vim));
       dst[1] = make_uint4((uint32_t)(w0 + h * stride + lane), __float_as_uint(wt[h]), 0u, 0u);
     }
@@ -414,9 +416,11 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
   if ((e = cudaMemcpyAsync(ws.cursor, ws.offsets, sizeof(uint32_t) * nb1, cudaMemcpyDeviceToDevice, s))) return e;
   const int nb = bins_per_row(p->n);
-  if ((e = cudaMemsetAsync(ws.binmag, 0, sizeof(float) * (size_t)(p->n_buckets / kColBlocks) * nb, s))) return e;
+  float *binmag = p->n >= kFixedMinN ? ws.binmag : nullptr;  // only long rows use the bound
+  if (binmag && (e = cudaMemsetAsync(binmag, 0, sizeof(float) * (size_t)(p->n_buckets / kColBlocks) * nb, s)))
+    return e;
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(vis, weight, ws.keyinfo, ws.cursor, p->n_vis,
-                                                              ws.records, ws.binmag, nb, p->W);
+                                                              ws.records, binmag, nb, p->W);
   p->launches += 1;
   return cudaGetLastError();
 }

@@ -68,7 +68,7 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   L.occ = off;
   off += align_up((size_t)p->n_planes * p->n);
   L.binmag = off;
-  off += align_up((size_t)(p->n_buckets / kColBlocks) * bins_per_row(p->n) * sizeof(float));
+  if (p->n >= kFixedMinN) off += align_up((size_t)(p->n_buckets / kColBlocks) * bins_per_row(p->n) * sizeof(float));
   L.comp = off;
   if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n * p->n * sizeof(float2));
   L.total = off;

@@ -20,6 +20,7 @@ constexpr uint32_t kDropKey = 0xFFFFFFFFu;
 // the sort sums max(|Re|, |Im|) of the weighted values whose W taps reach each bin of
 // kBinCols columns.
 constexpr int kBinCols = 64, kBinShift = 6;
+constexpr int kFixedMinN = 8192;  // image sizes whose rows use fixed-point accumulation
 __host__ __device__ constexpr int bins_per_row(int n) { return n >= kBinCols ? n / kBinCols : 1; }
 
 // counters[] slots in the workspace

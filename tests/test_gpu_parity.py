@@ -195,33 +195,42 @@ def test_grid_dense_tile_collisions(wst):
     assert rel_err(g.cpu().numpy(), ref) < TOL
 
 
-def test_grid_fixed_point_rows_are_deterministic(wst):
-    """Rows are accumulated in fixed point (integer atomics): the sums do not depend on the
-    order of the additions, so two gridding passes agree bit for bit."""
-    u, v, w, vis = make_case(n=512, n_vis=60000, seed=9)
-    cfg = wst.Config(n=512, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0)
+def test_grid_coherent_pileup_regrids_in_float(wst):
+    """2000 identical visibilities on one cell centre, in a row whose other 8000
+    visibilities spread over the columns: the row takes the fixed-point path (its busiest
+    bin is not dominant), the pile-up exceeds the int32 range of the fine quantum, the
+    kernel detects it and accumulates the row again in float; planes and image match the
+    oracle."""
+    rng = np.random.default_rng(13)
+    n, fov, npile, nrow, nrest = 8192, 0.1, 2000, 8000, 3000  # fixed-point rows need n >= 8192
+    u = np.concatenate([np.full(npile, 300.0), rng.uniform(-40000.0, 40000.0, nrow),
+                        rng.uniform(-40000.0, 40000.0, nrest)]).astype(np.float32)
+    v = np.concatenate([np.full(npile + nrow, -150.0), rng.uniform(-40000.0, 40000.0, nrest)]).astype(np.float32)
+    w = rng.uniform(-10.0, 10.0, u.size).astype(np.float32)
+    vis = np.concatenate([np.full(npile, 1.0 + 0.5j, np.complex64),
+                          synth.random_visibilities(nrow + nrest, rng)]).astype(np.complex64)
+    cfg = wst.Config(n=n, fov=fov, n_w=1, w_min=-10.0, w_max=10.0)
     plan = gpu_plan(wst, cfg, u, v, w, vis)
-    g1 = torch.empty((3, 512, 512), dtype=torch.complex64, device="cuda")
-    g2 = torch.empty_like(g1)
-    wst.wst_grid(plan.handle, 0, 3, g1)
-    wst.wst_grid(plan.handle, 0, 3, g2)
-    assert torch.equal(g1.view(torch.int64), g2.view(torch.int64))
-    ref = oracle.grid(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis)
-    assert rel_err(g1.cpu().numpy(), ref) < TOL
+    g = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_grid(plan.handle, 0, 1, g)
+    oc = ocfg_for(cfg, -10.0, 10.0)
+    assert rel_err(g.cpu().numpy(), oracle.grid(oc, u, v, w, vis)) < TOL
+    img = plan.image(flags=wst.WST_NO_CORRECTION)
+    assert rel_err(img[0].cpu().numpy(), oracle.image(oc, u, v, w, vis, correct=False)) < TOL
 
 
 def test_grid_and_image_dense_rows_keep_float_atomics(wst):
-    """A row whose busiest 64-column bin holds more than 512 times the row's mean
-    magnitude per visibility-row keeps float atomics (here 1.1M visibility-rows over four
+    """A row whose busiest 64-column bin holds more than 8192 times the row's mean
+    magnitude per visibility-row keeps float atomics (here 1.1M visibility-rows over seven
     bins); a plane holding such rows and ordinary (fixed-point) ones matches the oracle,
     gridded and imaged."""
     rng = np.random.default_rng(5)
-    n, fov, nd, ns = 256, 0.1, 1_100_000, 4000
-    u = np.concatenate([rng.uniform(-1200.0, 1200.0, nd), rng.uniform(-1200.0, 1200.0, ns)]).astype(np.float32)
-    v = np.concatenate([np.zeros(nd), rng.uniform(-1200.0, 1200.0, ns)]).astype(np.float32)
+    n, fov, nd, ns = 8192, 0.1, 1_100_000, 40000  # fixed-point rows need n >= 8192
+    u = np.concatenate([rng.uniform(-2000.0, 2000.0, nd), rng.uniform(-40000.0, 40000.0, ns)]).astype(np.float32)
+    v = np.concatenate([np.zeros(nd), rng.uniform(-40000.0, 40000.0, ns)]).astype(np.float32)
     w = rng.uniform(-10.0, 10.0, nd + ns).astype(np.float32)
     vis = synth.random_visibilities(nd + ns, rng)
-    cfg = wst.Config(n=n, fov=fov, n_w=1, w_min=-10.0, w_max=10.0)  # rows 125..131: 1.1M each
+    cfg = wst.Config(n=n, fov=fov, n_w=1, w_min=-10.0, w_max=10.0)  # rows 4093..4099: 1.1M each
     plan = gpu_plan(wst, cfg, u, v, w, vis)
     g = torch.empty((1, n, n), dtype=torch.complex64, device="cuda")
     wst.wst_grid(plan.handle, 0, 1, g)
