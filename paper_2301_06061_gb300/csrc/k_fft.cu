@@ -263,7 +263,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // warp-uniform.  The factors w_N^{a c} of a tile come from a shared table filled one
 // tile ahead (three in rotation).
 template <int LB, int DIR, bool TW_FIRST>
-__global__ void __launch_bounds__(LB / 16 * 32, (LB == 128 ? 512 : 768) / (LB / 16 * 32))
+__global__ void __launch_bounds__(LB / 16 * 32, 512 / (LB / 16 * 32))
 k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
   constexpr int CB = 32, EPT = 16, TPL = LB / EPT, THREADS = TPL * CB;
   constexpr int R1 = LB / 16;  // radix of the second stage
