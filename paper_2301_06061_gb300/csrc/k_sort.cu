@@ -21,11 +21,6 @@ __device__ __forceinline__ uint32_t float_to_ordered(float f) {
 
 __device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-__device__ __forceinline__ void warp_count(unsigned long long *ctr, bool pred) {
-  unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
-}
-
 // per image min / max of the finite w (order-preserving integer encoding)
 __global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax) {
   const int img = blockIdx.y;
@@ -64,9 +59,18 @@ struct SortGeom {
 // otherwise (a few visibilities in 10^7).
 
 // FP64 reference placement of one visibility (the rare path)
-__device__ __noinline__ void place_fp64(float uf, float vf, float wf, const SortGeom &g, double w_lo, double scale,
-                                        int &ci_out, int &cj_out, int &k_out, bool &dropped, uint32_t &fx,
-                                        uint32_t &fy) {
+struct Placement {
+  int ci, cj, k;
+  uint32_t fx, fy;
+  bool dropped;
+};
+
+__device__ __noinline__ Placement place_fp64(float uf, float vf, float wf, const SortGeom g, double w_lo,
+                                             double scale) {
+  Placement P;
+  int &ci_out = P.ci, &cj_out = P.cj, &k_out = P.k;
+  bool &dropped = P.dropped;
+  uint32_t &fx = P.fx, &fy = P.fy;
   const double x = __dadd_rn(g.half_n, __dmul_rn((double)uf, g.fov));
   const double y = __dadd_rn(g.half_n, __dmul_rn((double)vf, g.fov));
   const double hx = __dsub_rn(x, g.half_w), hy = __dsub_rn(y, g.half_w);
@@ -74,7 +78,7 @@ __device__ __noinline__ void place_fp64(float uf, float vf, float wf, const Sort
   dropped = ci < 0.0 || cj < 0.0 || ci + g.W > g.n || cj + g.W > g.n;
   ci_out = cj_out = k_out = 0;
   fx = fy = 0u;
-  if (dropped) return;
+  if (dropped) return P;
   if (scale > 0.0) {
     const double q = floor(__dmul_rn(__dsub_rn((double)wf, w_lo), scale));
     k_out = q < 0.0 ? 0 : (q > g.n_w - 1 ? g.n_w - 1 : (int)q);
@@ -85,6 +89,7 @@ __device__ __noinline__ void place_fp64(float uf, float vf, float wf, const Sort
   const double gx = __dsub_rn(ci, hx), gy = __dsub_rn(cj, hy);
   fx = (uint32_t)min(__double2uint_rn(gx * 16777216.0), 16777215u);
   fy = (uint32_t)min(__double2uint_rn(gy * 16777216.0), 16777215u);
+  return P;
 }
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
@@ -116,7 +121,7 @@ __device__ __forceinline__ void frac_ff(float hi, float lo, float &fl, float &e0
 }
 
 // pass 1: placement, bucket key, histogram rank (warp-aggregated atomics)
-__global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
+__global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, const float *__restrict__ v,
                        const float *__restrict__ w, const float2 *__restrict__ vis,
                        const float *__restrict__ weight, const int64_t *__restrict__ boff,
                        const double *__restrict__ wrange, const float4 *__restrict__ wrange_ff, SortGeom g,
@@ -130,6 +135,7 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
   const float nf = (float)g.n, wn = (float)g.W;
   // uniform trip count across the warp so that the warp-level votes are safe
   const int64_t start = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  uint32_t n_kept = 0, n_dropped = 0, n_nonfinite = 0;
   for (int64_t base = start; base < span; base += stride) {
     const int64_t jj = base + (threadIdx.x & 31);
     const bool in = jj < span;
@@ -192,7 +198,15 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
             fy = min(__float2uint_rn(fmaxf(gy, 0.0f) * 16777216.0f), 16777215u);
           }
         }
-        if (!sure) place_fp64(uf, vf, wf, g, wrange[4 * img + 0], wrange[4 * img + 1], ci, cj, k, dropped, fx, fy);
+        if (!sure) {
+          const Placement P = place_fp64(uf, vf, wf, g, wrange[4 * img + 0], wrange[4 * img + 1]);
+          ci = P.ci;
+          cj = P.cj;
+          k = P.k;
+          dropped = P.dropped;
+          fx = P.fx;
+          fy = P.fy;
+        }
         if (!dropped) {
           key = (uint32_t)((((int64_t)img * g.n_w + k) * g.n + cj) * kColBlocks + (int64_t)ci * kColBlocks / g.n);
           xpack = ((uint32_t)ci << 18) | (fx >> 6);
@@ -208,9 +222,18 @@ __global__ void k_keys(const float *__restrict__ u, const float *__restrict__ v,
       if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&offsets[key], (uint32_t)__popc(peers));
     }
     if (in) keyinfo[j] = make_uint4(key, 0u, xpack, ypack);
-    warp_count(&counters[CNT_KEPT], kept);
-    warp_count(&counters[CNT_DROPPED], dropped);
-    warp_count(&counters[CNT_NONFINITE], nonfinite);
+    n_kept += kept;
+    n_dropped += dropped;
+    n_nonfinite += nonfinite;
+  }
+  // the warp's counts, one reduction each
+  n_kept = __reduce_add_sync(0xFFFFFFFFu, n_kept);
+  n_dropped = __reduce_add_sync(0xFFFFFFFFu, n_dropped);
+  n_nonfinite = __reduce_add_sync(0xFFFFFFFFu, n_nonfinite);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_kept) atomicAdd(&counters[CNT_KEPT], (unsigned long long)n_kept);
+    if (n_dropped) atomicAdd(&counters[CNT_DROPPED], (unsigned long long)n_dropped);
+    if (n_nonfinite) atomicAdd(&counters[CNT_NONFINITE], (unsigned long long)n_nonfinite);
   }
 }
 
