@@ -24,7 +24,8 @@
 // the rate of float ones on this GPU.  The sort leaves, per row bucket and bin of 64
 // columns, the sum of max(|Re|, |Im|) of the weighted values whose taps reach the bin;
 // for row q, M_b = the sum of bin b over the buckets j0 = q - W + 1 ... q bounds every
-// cell of bin b by M_b G^2 (G the largest |kernel value|).  With B = max_b M_b G^2 the
+// cell of bin b by M_b G^2 (G the largest |kernel value|); the sort's last pass
+// (k_row_bounds) leaves max_b M_b and sum_b M_b per row.  With B = max_b M_b G^2 the
 // row is accumulated in int32 units of delta = B / 2^34: each tap is rounded to a
 // multiple of delta (error <= delta/2).  B is a sum of magnitudes, far above the cells
 // of a dense bin (random phases add up like a square root), which is what makes the
@@ -123,35 +124,42 @@ __device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re,
 // range bnd[0] .. bnd[d_lo + 1] is split evenly over the row's threads, one visibility
 // per thread (two in flight); bnd[i] is where row j0 = q - d_lo + i starts.  WT > 0
 // fixes the support at compile time.
+__device__ __forceinline__ void cp_async16_rg(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
 template <int N, int WT, bool FIXED>
 __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__restrict__ rec,
                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
-                                        float qscale) {
+                                        float qscale, RecHead *stg, int stg_stride) {
   constexpr int TPR = RowCfg<N>::TPR;
   int ovf = 0;
   const uint32_t s_end = bnd[d_lo + 1];
   if constexpr (WT > 0) {
     const float q = expf(-2.0f * kp.inv2s2);
-    for (uint32_t s = bnd[0] + jt; s < s_end; s += 2 * TPR) {
-      const uint32_t sp[2] = {s, s + TPR};
-      const bool two = sp[1] < s_end;
-      RecHead r[2];
-      r[0] = rec_head(rec, sp[0]);
-      if (two) r[1] = rec_head(rec, sp[1]);
+    // this thread's record heads are copied into its own two shared slots one record
+    // ahead (cp.async), so the next load is in flight while a record is gridded
+    const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(stg);
+    const uint32_t slot1 = (uint32_t)__cvta_generic_to_shared(stg + stg_stride);
+    uint32_t s = bnd[0] + jt;
+    if (s < s_end) cp_async16_rg(slot0, rec + s);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int k = 0; s < s_end; ++k, s += TPR) {
+      if (s + TPR < s_end) cp_async16_rg((k & 1) ? slot0 : slot1, rec + s + TPR);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const RecHead r = (k & 1) ? stg[stg_stride] : stg[0];
+      int i = d_lo;
+      while (s < bnd[i]) --i;  // the last row starting at or before the record
+      const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
+      float g[WT];
+      x_taps<WT>(kp, rec_gx(r), q, g);
+      const int i0 = rec_i0(r);
+      const float vre = r.vre * gy, vim = r.vim * gy;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !two) break;
-        int i = d_lo;
-        while (sp[h] < bnd[i]) --i;  // the last row starting at or before the record
-        const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r[h]));
-        float g[WT];
-        x_taps<WT>(kp, rec_gx(r[h]), q, g);
-        const int i0 = rec_i0(r[h]);
-        const float vre = r[h].vre * gy, vim = r[h].vim * gy;
-#pragma unroll
-        for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale, ovf);
-      }
+      for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale, ovf);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else {
     const int W = kp.support;
     for (uint32_t s = bnd[0] + jt; s < s_end; s += TPR) {
@@ -176,8 +184,8 @@ template <int N, bool FFT, int WT>
 __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const Record *__restrict__ rec,
                                              const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
                                              const KernelParams &kp, float2 *__restrict__ orow,
-                                             const float2 *twt, int jt, const float *__restrict__ binmag,
-                                             float g2, uint32_t *red) {
+                                             const float2 *twt, int jt, const float2 *__restrict__ rowbound,
+                                             float g2, RecHead *stg, int stg_stride) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -187,38 +195,17 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   const int W = WT > 0 ? WT : kp.support;
   float *sre = reinterpret_cast<float *>(srow), *sim = sre + N;  // planar accumulation
   const int d_lo = min(q, W - 1);
-  constexpr int NB = bins_per_row(N);
-  float bmax = 0.0f, btot = 0.0f;  // this thread's bins: largest and total magnitude sum
+  // the row's largest bin sum and total of the bin sums (k_row_bounds), broadcast
+  float2 mb = make_float2(0.0f, 0.0f);
   if (nonempty) {
     for (int i = jt; i <= d_lo + 1; i += TPR) bnd[i] = off[(b0 + q - d_lo + i) * kColBlocks];
-    if constexpr (kFixedRows<N>)
-      for (int b = jt; b < NB; b += TPR) {
-      float m = 0.0f;
-      for (int d = 0; d <= d_lo; ++d) m += __ldg(binmag + (size_t)(b0 + q - d) * NB + b);
-      bmax = fmaxf(bmax, m);
-      btot += m;
-    }
+    if constexpr (kFixedRows<N>) mb = __ldg(rowbound + b0 + q);
   }
-  if (jt == 0) red[0] = red[1] = 0u;
   zero_row<N>(srow, jt);
   __syncthreads();
-  if (kFixedRows<N> && nonempty) {  // row maximum and total (non-negative floats order like their bits)
-    if constexpr (TPR >= 32) {
-      for (int o = 16; o > 0; o >>= 1) btot += __shfl_xor_sync(0xFFFFFFFFu, btot, o);
-      const uint32_t mb = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bmax));
-      if ((jt & 31) == 0) {
-        atomicMax(&red[0], mb);
-        atomicAdd(reinterpret_cast<float *>(&red[1]), btot);
-      }
-    } else {
-      atomicMax(&red[0], __float_as_uint(bmax));
-      atomicAdd(reinterpret_cast<float *>(&red[1]), btot);
-    }
-  }
-  if constexpr (kFixedRows<N>) __syncthreads();
   // the same decision and quantum in every thread of the row
   const uint32_t cnt = nonempty ? bnd[d_lo + 1] - bnd[0] : 0u;
-  const float mmax = __uint_as_float(red[0]), mtot = __uint_as_float(red[1]);
+  const float mmax = mb.x, mtot = mb.y;
   const float bound = mmax * g2;
   // n_eff: the busiest bin's magnitude in units of the row's mean per visibility-row
   const float n_eff = mmax * (float)cnt * (1.0f + (float)(W - 1) / (float)kBinCols) / fmaxf(mtot, 0x1p-126f);
@@ -230,8 +217,8 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   bool fx = fixed;
   int ovf = 0;
   if (nonempty) {
-    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit));
-    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f);
+    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit), stg, stg_stride);
+    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, stg, stg_stride);
   }
   bool redo = false;  // a tap or a partial sum left the int32 range: accumulate in float
   if constexpr (kFixedRows<N>) redo = __syncthreads_or(ovf < 0);
@@ -239,7 +226,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   if (redo) {
     zero_row<N>(srow, jt);
     __syncthreads();
-    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f);
+    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, stg, stg_stride);
     fx = false;
     __syncthreads();
   }
@@ -296,17 +283,19 @@ template <int N, bool FFT, int WT>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
 k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int np,
             KernelParams kp, float2 *__restrict__ out, uint8_t *__restrict__ occ,
-            unsigned long long *__restrict__ counter, Tw tw, const float *__restrict__ binmag) {
+            unsigned long long *__restrict__ counter, Tw tw, const float2 *__restrict__ rowbound) {
   using C = RowCfg<N>;
   constexpr int TPR = C::TPR, RPC = C::RPC;
   extern __shared__ __align__(16) float2 sm_rows[];
   __shared__ long long s_item;
   __shared__ uint32_t s_bnd[RPC][kMaxSupport + 2];
   __shared__ uint32_t s_gmax;  // largest |kernel value| (FP32 bits)
-  __shared__ uint32_t s_red[RPC][2];  // per row: largest bin magnitude (bits), total (float)
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
   float2 *twt = sm_rows + RPC * C::PADL;  // twiddle tables (visible after the first barrier)
+  // two record-head slots per thread after the tables
+  RecHead *stg = reinterpret_cast<RecHead *>(twt + (FFT ? line_table_size<N, C::EPT, TPR>() : 0)) + threadIdx.x;
+  const int stg_stride = C::THREADS;
   if constexpr (FFT) fill_line_tables<N, C::EPT, TPR>(twt, tw);
   // G^2 of the fixed-point bound (G = 1 for the Gaussian and the ES kernel, the largest
   // |sample| of a table: linear interpolation stays below it)
@@ -362,7 +351,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const long long item = base + (e >> 1);
         const int pl = (int)(item / N), q = (int)(item % N);
         grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
-                                 out + ((int64_t)pl * N + q) * N, twt, jt, binmag, g2, s_red[0]);
+                                 out + ((int64_t)pl * N + q) * N, twt, jt, rowbound, g2, stg, stg_stride);
       }
     }
   } else {
@@ -380,7 +369,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
       grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt,
-                               binmag, g2, s_red[rl]);
+                               rowbound, g2, stg, stg_stride);
     }
   }
 }
@@ -540,7 +529,8 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
   auto kern = !FFT ? k_grid_rows<N, FFT, 0>
               : p->cfg.support == 7 ? k_grid_rows<N, FFT, 7>
               : p->cfg.support == 8 ? k_grid_rows<N, FFT, 8> : k_grid_rows<N, FFT, 0>;
-  const size_t smem = sizeof(float2) * (C::RPC * C::PADL + (FFT ? line_table_size<N, C::EPT, C::TPR>() : 0));
+  const size_t smem = sizeof(float2) * (C::RPC * C::PADL + (FFT ? line_table_size<N, C::EPT, C::TPR>() : 0)) +
+                      2 * C::THREADS * sizeof(RecHead);
   int grid = 0;
   cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
   if (e != cudaSuccess) return e;
@@ -548,7 +538,7 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
   kern<<<grid, C::THREADS, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, np, kernel_params(p), out,
-                                             p->W_.occ, counter, tw_half(p), p->W_.binmag);
+                                             p->W_.occ, counter, tw_half(p), p->W_.rowbound);
   return cudaGetLastError();
 }
 

@@ -394,6 +394,34 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
   }
 }
 
+// Per grid row q of every (image, plane): over the column bins b, the largest and the
+// total of M_b = sum of bin b of the buckets j0 = q - W + 1 ... q (one warp per row; rows
+// no visibility reaches get zeros).  The fused row kernel takes its fixed-point quantum
+// from them.
+__global__ void k_row_bounds(const float *__restrict__ binmag, const uint32_t *__restrict__ offsets,
+                             int64_t n_rows, int n, int nb, int W, float2 *__restrict__ rowbound) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_rows; r += warps) {
+    const int q = (int)(r % n);
+    const int d_lo = min(q, W - 1);
+    float mmax = 0.0f, mtot = 0.0f;
+    if (offsets[(r - d_lo) * kColBlocks] != offsets[(r + 1) * kColBlocks]) {
+      for (int b = lane; b < nb; b += 32) {
+        float m = 0.0f;
+        for (int d = 0; d <= d_lo; ++d) m += binmag[(size_t)(r - d) * nb + b];
+        mmax = fmaxf(mmax, m);
+        mtot += m;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mmax = fmaxf(mmax, __shfl_xor_sync(0xFFFFFFFFu, mmax, o));
+        mtot += __shfl_xor_sync(0xFFFFFFFFu, mtot, o);
+      }
+    }
+    if (lane == 0) rowbound[r] = make_float2(mmax, mtot);
+  }
+}
+
 static unsigned grid_for(int64_t n, int threads, int max_blocks) {
   int64_t b = (n + threads - 1) / threads;
   if (b > max_blocks) b = max_blocks;
@@ -445,6 +473,12 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(vis, weight, ws.keyinfo, ws.cursor, p->n_vis,
                                                               ws.records, binmag, nb, p->W);
   p->launches += 1;
+  if (binmag) {
+    const int64_t n_rows = p->n_buckets / kColBlocks;
+    k_row_bounds<<<grid_for(n_rows * 32, 256, 152 * 8), 256, 0, s>>>(binmag, ws.offsets, n_rows, p->n, nb, p->W,
+                                                                     ws.rowbound);
+    p->launches += 1;
+  }
   return cudaGetLastError();
 }
 

@@ -43,7 +43,7 @@ int ilog2(int x) {
 }
 
 struct Layout {
-  size_t keyinfo_planes, records, offsets, cursor, scan_tmp, counters, wminmax, occ, binmag, comp, total;
+  size_t keyinfo_planes, records, offsets, cursor, scan_tmp, counters, wminmax, occ, binmag, rowbound, comp, total;
 };
 
 Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
@@ -69,6 +69,8 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   off += align_up((size_t)p->n_planes * p->n);
   L.binmag = off;
   if (p->n >= kFixedMinN) off += align_up((size_t)(p->n_buckets / kColBlocks) * bins_per_row(p->n) * sizeof(float));
+  L.rowbound = off;
+  if (p->n >= kFixedMinN) off += align_up((size_t)(p->n_buckets / kColBlocks) * sizeof(float2));
   L.comp = off;
   if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n * p->n * sizeof(float2));
   L.total = off;
@@ -288,6 +290,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   W.wminmax = (uint32_t *)(p->ws + L.wminmax);
   W.occ = (uint8_t *)(p->ws + L.occ);
   W.binmag = (float *)(p->ws + L.binmag);
+  W.rowbound = (float2 *)(p->ws + L.rowbound);
   W.comp = (p->chunk < p->n_planes) ? (float2 *)(p->ws + L.comp) : nullptr;
   W.bytes = L.total;
   p->launches = 0;

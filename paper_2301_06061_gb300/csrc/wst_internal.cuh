@@ -86,6 +86,7 @@ struct Workspace {
   uint32_t *wminmax;   // per image: ordered-int min and max of finite w
   uint8_t *occ;        // per (plane of the chunk, row): 1 if any visibility reaches the row
   float *binmag;       // per (row bucket, column bin): magnitude sum (fixed-point bound)
+  float2 *rowbound;    // per grid row: (largest bin sum, total of the bin sums) over its W buckets
   float2 *planes;      // chunk of planes
   float2 *comp;        // Kahan compensation image [batch][N*N]
   size_t bytes;
