@@ -150,9 +150,12 @@ wst_status wst_plan_set_workspace(wst_plan plan, void *device_ptr, size_t bytes)
 wst_status wst_plan_set_kernel_table(wst_plan plan, const float *table_dev);
 
 /*
- * Bind visibilities and bucket-sort them (device) by (image, plane, 64x64 tile).
+ * Bind visibilities and bucket-sort them (device) by (image, plane, row of the first tap).
  * u, v, w: FP32 [n_vis] wavelengths; vis: complex64 [n_vis]; weight: FP32 [n_vis]
- * or NULL (natural weights 1).  batch_offsets: HOST int64 [batch + 1], image i
+ * or NULL (natural weights 1).  The arrays may be device memory or page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister): the sort kernels then read them in place
+ * through the host mapping (on GB300 over NVLink-C2C), with no separate copy; pageable
+ * host memory only where the device reports cudaDevAttrPageableMemoryAccess.  batch_offsets: HOST int64 [batch + 1], image i
  * owns visibilities [off[i], off[i+1]) (NULL allowed when batch == 1).  The
  * plane range is taken from the config or, if w_min == w_max, from the min/max
  * of the finite w of each image.  The inputs are read during this call's stream
@@ -184,7 +187,9 @@ wst_status wst_correct(wst_plan plan, void *image_inout);
 /*
  * The whole hot path (Eq. 2-3): grid, FFT, phase screen and plane sum for every
  * plane of every image, then the grid correction (unless WST_NO_CORRECTION).
- * image_out: complex64 [batch x N x N], overwritten.  Planes are processed in
+ * image_out: complex64 [batch x N x N], overwritten; device memory or page-locked
+ * host memory, which the last column pass then writes in place (on GB300 over
+ * NVLink-C2C) with no separate copy.  Planes are processed in
  * chunks of planes_per_chunk held in the workspace; with WST_FLAG_KAHAN the
  * plane sum is compensated on chip within a chunk and across chunks.
  */

@@ -258,12 +258,45 @@ wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
   return WST_OK;
 }
 
+// The address the kernels use for a caller's array, or NULL if the device cannot reach
+// it: device or managed memory as is; page-locked host memory through its mapping into
+// the device's address space (on GB300 the accesses cross NVLink-C2C: the kernels read
+// the inputs and write the image in place, no separate copy); pageable host memory only
+// where the device reports cudaDevAttrPageableMemoryAccess.
+static const void *device_view(const wst_plan_s *p, const void *ptr) {
+  if (!ptr) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  int pageable = 0;
+  if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return pageable ? ptr : nullptr;
+}
+
 wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const float *v, const float *w,
                             const void *vis, const float *weight, const int64_t *batch_offsets) {
   if (!p) return WST_ERR_INVALID_ARG;
   p->vis_set = false;
   if (n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return fail(p, WST_ERR_INVALID_ARG, "n_vis out of range");
   if (n_vis > 0 && (!u || !v || !w || !vis)) return fail(p, WST_ERR_INVALID_ARG, "NULL visibility array");
+  if (n_vis > 0) {
+    const void *du = device_view(p, u), *dv = device_view(p, v), *dw = device_view(p, w);
+    const void *dvis = device_view(p, vis), *dwt = weight ? device_view(p, weight) : nullptr;
+    if (!du || !dv || !dw || !dvis || (weight && !dwt))
+      return fail(p, WST_ERR_INVALID_ARG, "visibility arrays must be device or page-locked host memory");
+    u = (const float *)du;
+    v = (const float *)dv;
+    w = (const float *)dw;
+    vis = dvis;
+    weight = (const float *)dwt;
+  }
   if (p->batch > 1 && !batch_offsets) return fail(p, WST_ERR_INVALID_ARG, "batch offsets required");
   std::vector<int64_t> off(p->batch + 1);
   if (batch_offsets) {
@@ -356,7 +389,8 @@ wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
   if (flags & ~WST_NO_CORRECTION) return fail(p, WST_ERR_INVALID_ARG, "unknown flags");
   const bool correct = !(flags & WST_NO_CORRECTION);
   const bool kahan = (p->cfg.flags & WST_FLAG_KAHAN) != 0;
-  float2 *img = (float2 *)image_out;
+  float2 *img = (float2 *)device_view(p, image_out);
+  if (!img) return fail(p, WST_ERR_INVALID_ARG, "image must be device or page-locked host memory");
   float2 *planes = p->W_.planes;
   p->n_chunks = 0;
   p->launches = 0;

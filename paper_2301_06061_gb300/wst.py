@@ -120,12 +120,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     return _lib
 
 
-def _ptr(t):
+def _ptr(t, host_ok: bool = False):
+    """Device pointer of a CUDA tensor; with host_ok, also a page-locked CPU tensor (the
+    entry points that accept host memory read or write it in place)."""
     if t is None:
         return None
     if isinstance(t, torch.Tensor):
-        if not t.is_cuda:
-            raise ValueError("libwst takes CUDA tensors")
+        if not t.is_cuda and not (host_ok and t.is_pinned()):
+            raise ValueError("libwst takes CUDA tensors" + (" or pinned CPU tensors" if host_ok else ""))
         if not t.is_contiguous():
             raise ValueError("libwst takes contiguous tensors")
         return ctypes.c_void_p(t.data_ptr())
@@ -201,7 +203,9 @@ def wst_plan_set_vis(plan, u, v, w, vis, weight=None, batch_offsets=None) -> Non
     if batch_offsets is not None:
         arr = (ctypes.c_int64 * len(batch_offsets))(*[int(x) for x in batch_offsets])
         off = ctypes.cast(arr, ctypes.c_void_p)
-    _check(load_library().wst_plan_set_vis(plan, n, _ptr(u), _ptr(v), _ptr(w), _ptr(vis), _ptr(weight), off),
+    h = True  # device tensors or pinned host tensors
+    _check(load_library().wst_plan_set_vis(plan, n, _ptr(u, h), _ptr(v, h), _ptr(w, h), _ptr(vis, h),
+                                           _ptr(weight, h), off),
            "wst_plan_set_vis", plan)
 
 
@@ -221,7 +225,7 @@ def wst_correct(plan, image_inout) -> None:
 
 def wst_image(plan, image_out: torch.Tensor, flags: int = 0) -> None:
     assert image_out.dtype == torch.complex64
-    _check(load_library().wst_image(plan, _ptr(image_out), flags), "wst_image", plan)
+    _check(load_library().wst_image(plan, _ptr(image_out, True), flags), "wst_image", plan)
 
 
 def wst_degrid(plan, dimage: torch.Tensor, dvis_out: torch.Tensor, flags: int = 0) -> None:

@@ -278,6 +278,37 @@ def test_image_end_to_end(wst, n, n_w, chunk, flags):
     assert plan.stats()["n_chunks"] == (-(-n_w // chunk) if chunk else 1)
 
 
+@pytest.mark.parametrize("n", [256, 8192])
+def test_image_from_pinned_host_buffers_in_place(wst, n):
+    """Page-locked host arrays go straight to wst_plan_set_vis and a page-locked host
+    image to wst_image: the kernels read and write them in place.  The image matches the
+    oracle and the image computed from device copies of the same arrays."""
+    u, v, w, vis = make_case(n=n, n_vis=4000, seed=31 + n)
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    plan = wst.Plan(cfg)
+    plan.set_vis(pin(u), pin(v), pin(w), pin(vis))
+    host_img = torch.empty((1, n, n), dtype=torch.complex64).pin_memory()
+    plan.image(out=host_img)
+    torch.cuda.synchronize()
+    assert plan.stats()["n_kept"] == int((oracle.locate(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis)[3] == 0).sum())
+    ref = oracle.image(ocfg_for(cfg, -200.0, 200.0), u, v, w, vis)
+    assert_image_parity(host_img[0].numpy(), ref, ocfg_for(cfg, -200.0, 200.0))
+    # uncorrected images (the correction amplifies rounding at the corners): the two
+    # differ only by the order of the float atomics
+    plan.image(out=host_img, flags=wst.WST_NO_CORRECTION)
+    torch.cuda.synchronize()
+    dev_img = gpu_plan(wst, cfg, u, v, w, vis).image(flags=wst.WST_NO_CORRECTION)[0].cpu().numpy()
+    assert rel_err(host_img[0].numpy(), dev_img) < 1e-6
+
+
+def test_pageable_or_foreign_host_tensors_rejected_by_binding(wst):
+    with pytest.raises(ValueError):
+        wst._ptr(torch.zeros(4), True)  # not page-locked
+    with pytest.raises(ValueError):
+        wst._ptr(torch.zeros(4).pin_memory())  # host memory where only device memory is accepted
+
+
 @pytest.mark.parametrize("kernel,W,param", [("es", 8, 2.3 * 8), ("gauss", 8, 0.925), ("table", 8, None)])
 def test_image_kernels(wst, kernel, W, param):
     n = 256
