@@ -447,8 +447,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     bytes_launch = stage_bytes(dom, work.n, planes, st["n_chunks"], batch, st["n_kept"], n_vis)
     peak, peak_src = load_peaks()
     achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
-    kernel_names = {"sort": "k_keys+k_scan+k_scatter", "grid": "k_grid_rows (gridding + row FFT)", "rows": "k_rows",
-                    "cols_a": "k_cols_a", "cols_b": "k_cols_b_acc"}
+    kernel_names = {"sort": "k_keys+k_scan+k_scatter+k_row_bounds", "grid": "k_grid_rows (gridding + row FFT)",
+                    "rows": "k_rows", "cols_a": "k_cols_a16 (column stage A)",
+                    "cols_b": "k_cols_b16 (column stage B + phase screen + Kahan plane sum)"}
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": profiled_traffic(dom, args.workload, 1.0),
