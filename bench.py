@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--snap-w", action="store_true",
                     help="place every w on its plane centre, so the error against the direct transform is "
                          "the (u,v) kernel's alone (kernel comparisons)")
+    ap.add_argument("--wfold", action="store_true",
+                    help="mirror w < 0 visibilities (WST_FLAG_WFOLD): half the w range; the real part is the image")
     ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8"], default="gauss",
                     help="gauss: W=7 Gaussian (the paper's); gauss8 / learned: W=8 Gaussian or the trained "
                          "table (paper_2301_06061_gb300/data/learned_kernel_w8.npz)")
@@ -142,11 +144,13 @@ def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np
 
 
 def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev, n_pix: int, kernel: str,
-                   support: int, sigma: float, table):
+                   support: int, sigma: float, table, wfold: bool = False):
     """The image against the direct transform (GPU, float-float phases) at the brightest
     sources' pixels and at seeded random pixels, with the per-pixel bound
     B = sum|V| (min(2, 2 pi dmax |n - 1|) + e_a + e_b + e_a e_b) + 1e-5 peak, dmax the
-    largest distance of a w from its plane centre and e the kernel error above."""
+    largest distance of a w from its plane centre and e the kernel error above.  With
+    w-folding the real parts are compared (the folded image's real part is the dirty
+    image) and the plane offsets are those of |w|."""
     n, fov = work.n, work.fov
     sky = work.sky
     order = np.argsort(-sky.flux)[: n_pix // 2]
@@ -162,13 +166,17 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     dft = torch.empty(pa.size, dtype=torch.complex64, device=dev)
     wst.wst_dft(d_u, d_v, d_w, d_vis, n, fov, d_pa, d_pb, dft)
     got = img[0][d_pb.long(), d_pa.long()]
-    err = (got - dft).abs().double().cpu().numpy()
-    dft_abs = dft.abs().double().cpu().numpy()
+    if wfold:
+        err = (got.real - dft.real).abs().double().cpu().numpy()
+        dft_abs = dft.real.abs().double().cpu().numpy()
+    else:
+        err = (got - dft).abs().double().cpu().numpy()
+        dft_abs = dft.abs().double().cpu().numpy()
     peak = dft_abs.max()
     sum_abs = float(d_vis.abs().double().sum().item())
     # largest |w - w_k| over the data, w_k the centre of the plane the visibility lands on
     lo, hi = float(plan_stats["w_min"]), float(plan_stats["w_max"])
-    w64 = d_w.double()
+    w64 = d_w.double().abs() if wfold else d_w.double()
     k = torch.clamp(torch.floor((w64 - lo) * (work.n_w / (hi - lo))), 0, work.n_w - 1)
     dmax = float((w64 - (lo + (k + 0.5) * (hi - lo) / work.n_w)).abs().max().item())
     la = (pa - n // 2) * fov / n
@@ -388,7 +396,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         table = torch.from_numpy(tab_np).to(dev)
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
     cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
-                     flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING, planes_per_chunk=args.chunk, batch=batch,
+                     flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING | (wst.WST_FLAG_WFOLD if args.wfold else 0),
+                     planes_per_chunk=args.chunk, batch=batch,
                      **kcfg)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_u, h_v, h_w = pin(work.u), pin(work.v), pin(work.w)
@@ -513,14 +522,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.dft_pixels > 0 and batch == 1:
         sigma = kcfg.get("kparam", 0.0)
         acc = accuracy_block(torch, wst, work, st, d_u, d_v, d_w, d_vis, img, dev, args.dft_pixels,
-                             args.kernel, cfg.support, sigma, None if table is None else tab_np)
+                             args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and batch == 1:
         job_s, sample, cores, osample = time_oracle_sample(work, vis_np)
         cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
                "sample": sample}
-        if args.kernel == "gauss" and not args.snap_w:  # same kernel as the oracle's sample
+        if args.kernel == "gauss" and not args.snap_w and not args.wfold:  # the oracle sample's setting
             cpu["parity_vs_oracle"] = oracle_parity(torch, wst, dev, osample)
 
     clocks = clk.summary()
@@ -530,7 +539,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
-                       "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w, "planes_per_chunk": args.chunk or planes,
+                       "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w,
+                       "wfold": args.wfold, "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},

@@ -73,6 +73,14 @@ enum {
 #define WST_FLAG_KAHAN 0x1u       /* compensated (Kahan) accumulation of the planes   */
 #define WST_FLAG_FP64_SCREEN 0x2u /* phase argument in native FP64, not float-float   */
 #define WST_FLAG_TIMING 0x4u      /* record per-stage CUDA-event times in wst_image   */
+/* WST_FLAG_WFOLD: every visibility with w < 0 is replaced by its Hermitian mirror
+ * (u, v, w, V) -> (-u, -v, -w, conj V) before placement, so the planes only span
+ * [min |w|, max |w|] (half the usual range: half the plane spacing at the same N_w).
+ * A mirrored visibility contributes the complex conjugate of its original term to
+ * Eq. 2, so Re(image) is the dirty image of the original visibilities and Im(image)
+ * is not.  Not in the paper (a known variant of w-stacking).  wst_degrid and
+ * wst_kernel_grad return WST_ERR_UNSUPPORTED with it (the map is only real-linear). */
+#define WST_FLAG_WFOLD 0x8u
 
 /* per-call flags of wst_image / wst_correct / wst_degrid / wst_kernel_grad */
 #define WST_NO_CORRECTION 0x1u /* omit the 1/(Ghat(nu_a) Ghat(nu_b)) grid correction */

@@ -15,6 +15,7 @@ from .oracle import (  # noqa: F401
     dft_pixels,
     fft1d,
     fft2_centered,
+    fold_w,
     gauss_legendre,
     grid,
     image,

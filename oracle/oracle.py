@@ -16,13 +16,16 @@ Every function follows a passage of arXiv:2301.06061:
                        the paper's conclusions)
 * ``kernel_grad``   -- gradient of a real loss w.r.t. a tabulated kernel
 * ``kernel_ft``     -- Ghat(nu), the Fourier transform of the truncated kernel
+* ``fold_w``        -- the w-folding variant's Hermitian mirror of w < 0 visibilities
+                       (not in the paper; applied to the inputs of the functions above)
 
 Pins (tests/test_oracle_*.py) tie each one to something other than itself:
 numpy/pocketfft and the textbook DFT for the FFT; closed forms for Ghat and the
 screen; brute-force DFT within the analytic aliasing bound for the image;
 linearity, Hermitian symmetry and the single-visibility flat image; the
 dot-product identity for the adjoint; finite differences for the kernel
-gradient; exact integer placement rules for ``locate``.
+gradient; exact integer placement rules for ``locate``; for ``fold_w``, the
+invariance of the real part of the direct transform.
 """
 from __future__ import annotations
 
@@ -138,6 +141,19 @@ class OracleConfig:
             cfg.ktable_len = 0
         self._cfg_keep = cfg
         return ctypes.byref(cfg)
+
+
+def fold_w(u, v, w, vis):
+    """The w-folding variant (not in the paper): every visibility with w < 0 replaced by
+    its Hermitian mirror (-u, -v, -w, conj V).  The mirrored term of the dirty image is
+    the complex conjugate of the original one, so the real part of the image is
+    unchanged.  Sign flips are exact in FP32; non-finite w are left alone."""
+    u, v, w = (np.array(a, dtype=np.float32, copy=True) for a in (u, v, w))
+    vis = np.array(vis, dtype=np.complex64, copy=True)
+    m = w < 0
+    u[m], v[m], w[m] = -u[m], -v[m], -w[m]
+    vis[m] = np.conj(vis[m])
+    return u, v, w, vis
 
 
 def resolve_w_range(w: np.ndarray, w_min: float, w_max: float) -> tuple[float, float]:

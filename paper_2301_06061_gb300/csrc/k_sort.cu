@@ -22,13 +22,15 @@ __device__ __forceinline__ uint32_t float_to_ordered(float f) {
 __device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfinite(a.y); }
 
 // per image min / max of the finite w (order-preserving integer encoding)
-__global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax) {
+// (fold: of |w|, the w of the mirrored visibilities)
+__global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax, bool fold) {
   const int img = blockIdx.y;
   const int64_t b0 = boff[img], b1 = boff[img + 1];
   uint32_t mn = 0xFFFFFFFFu, mx = 0u;
   for (int64_t j = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b1;
        j += (int64_t)gridDim.x * blockDim.x) {
     float x = w[j];
+    if (fold) x = fabsf(x);
     if (isfinite(x)) {
       uint32_t o = float_to_ordered(x);
       mn = min(mn, o);
@@ -125,7 +127,8 @@ __global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, co
                        const float *__restrict__ w, const float2 *__restrict__ vis,
                        const float *__restrict__ weight, const int64_t *__restrict__ boff,
                        const double *__restrict__ wrange, const float4 *__restrict__ wrange_ff, SortGeom g,
-                       uint32_t *offsets, uint4 *keyinfo, unsigned long long *counters) {
+                       uint32_t *offsets, uint4 *keyinfo, unsigned long long *counters,
+                       float4 *__restrict__ stash, bool fold) {
   const int img = blockIdx.y;
   const int64_t b0 = boff[img], b1 = boff[img + 1];
   const float4 wff = wrange_ff[img];  // w_lo (hi, lo), scale (hi, lo)
@@ -141,11 +144,18 @@ __global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, co
     const bool in = jj < span;
     const int64_t j = b0 + jj;
     bool nonfinite = false, dropped = false, kept = false;
-    uint32_t key = kDropKey, xpack = 0, ypack = 0;
+    uint32_t key = kDropKey, xpack = 0, ypack = 0, mirrored = 0;
     if (in) {
-      const float uf = u[j], vf = v[j], wf = w[j];
+      float uf = u[j], vf = v[j], wf = w[j];
+      if (fold && wf < 0.0f) {  // Hermitian mirror (exact sign flips); the scatter conjugates V
+        uf = -uf;
+        vf = -vf;
+        wf = -wf;
+        mirrored = 1;
+      }
       const float2 val = vis[j];
       const float wt = weight ? weight[j] : 1.0f;
+      if (stash) stash[j] = make_float4(val.x, val.y, wt, 0.0f);  // value and weight for the scatter
       if (!(isfinite(uf) && isfinite(vf) && isfinite(wf) && finite2(val) && isfinite(wt))) {
         nonfinite = true;
       } else {
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, co
       const unsigned peers = __match_any_sync(active, key);
       if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&offsets[key], (uint32_t)__popc(peers));
     }
-    if (in) keyinfo[j] = make_uint4(key, 0u, xpack, ypack);
+    if (in) keyinfo[j] = make_uint4(key, mirrored, xpack, ypack);
     n_kept += kept;
     n_dropped += dropped;
     n_nonfinite += nonfinite;
@@ -342,7 +352,8 @@ constexpr int kScatterIlp = 4;
 
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
                           const uint4 *__restrict__ keyinfo, uint32_t *__restrict__ cursor, int64_t n_vis,
-                          Record *__restrict__ records, float *__restrict__ binmag, int nb, int W) {
+                          Record *__restrict__ records, float *__restrict__ binmag, int nb, int W,
+                          const float4 *__restrict__ stash) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   // uniform trip count across the warp (warp-level votes below)
@@ -368,8 +379,14 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
     for (int h = 0; h < kScatterIlp; ++h) {
       const int64_t j = w0 + h * stride + lane;
       if (ki[h].x != kDropKey) {
-        val[h] = vis[j];
-        wt[h] = weight ? weight[j] : 1.0f;
+        if (stash) {
+          const float4 vw = stash[j];
+          val[h] = make_float2(vw.x, vw.y);
+          wt[h] = vw.z;
+        } else {
+          val[h] = vis[j];
+          wt[h] = weight ? weight[j] : 1.0f;
+        }
       }
     }
 #pragma unroll
@@ -379,7 +396,7 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
       if (!kept) continue;
       const uint32_t pos = b + __popc(peers[h] & ((1u << lane) - 1u));
       uint4 *dst = reinterpret_cast<uint4 *>(records + pos);
-      const float vre = val[h].x * wt[h], vim = val[h].y * wt[h];
+      const float vre = val[h].x * wt[h], vim = (ki[h].y ? -val[h].y : val[h].y) * wt[h];  // mirrored: conj
       const float mag = fmaxf(fabsf(vre), fabsf(vim));
       if (binmag) {
         const int i0 = (int)(ki[h].z >> 18);
@@ -430,7 +447,10 @@ static unsigned grid_for(int64_t n, int threads, int max_blocks) {
 }
 
 cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
-                              const float2 *vis, const float *weight) {
+                              const float2 *vis, const float *weight, bool host_inputs) {
+  // inputs in host memory are read once: the placement pass leaves value and weight in
+  // device memory for the scatter
+  float4 *stash = host_inputs ? p->W_.stash : nullptr;
   cudaStream_t s = p->stream;
   Workspace &ws = p->W_;
   const int64_t nb1 = p->n_buckets + 1;
@@ -444,8 +464,9 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   }
   const int64_t avg = p->n_vis / p->batch + 1;
   dim3 grd(grid_for(avg, 256, 4096), p->batch);
+  const bool fold = (p->cfg.flags & WST_FLAG_WFOLD) != 0;
   if (p->cfg.w_min == p->cfg.w_max) {
-    k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax);
+    k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax, fold);
     p->launches += 1;
   }
   if ((e = build_plane_centres(p))) return e;
@@ -461,7 +482,7 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   g.half_nf = (float)g.half_n;
   g.half_wf = (float)g.half_w;
   k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, p->wrange_ff, g, ws.offsets,
-                               ws.keyinfo, ws.counters);
+                               ws.keyinfo, ws.counters, stash, fold);
   p->launches += 1;
   if ((e = cudaGetLastError())) return e;
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;
@@ -471,7 +492,7 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   if (binmag && (e = cudaMemsetAsync(binmag, 0, sizeof(float) * (size_t)(p->n_buckets / kColBlocks) * nb, s)))
     return e;
   k_scatter<<<grid_for(p->n_vis, 256, 152 * 16), 256, 0, s>>>(vis, weight, ws.keyinfo, ws.cursor, p->n_vis,
-                                                              ws.records, binmag, nb, p->W);
+                                                              ws.records, binmag, nb, p->W, stash);
   p->launches += 1;
   if (binmag) {
     const int64_t n_rows = p->n_buckets / kColBlocks;

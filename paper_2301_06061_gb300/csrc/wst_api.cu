@@ -50,7 +50,7 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   Layout L;
   size_t off = 0;
   const size_t plane_bytes = (size_t)p->chunk * p->n * p->n * sizeof(float2);
-  const size_t keyinfo_bytes = (size_t)n_vis * sizeof(uint4);
+  const size_t keyinfo_bytes = (size_t)n_vis * (sizeof(uint4) + sizeof(float4));  // keys + value stash
   L.keyinfo_planes = off;
   off += align_up(plane_bytes > keyinfo_bytes ? plane_bytes : keyinfo_bytes);
   L.records = off;
@@ -164,7 +164,8 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
     return WST_ERR_INVALID_ARG;
   }
   if (c.batch < 1 || c.batch > 4096 || c.planes_per_chunk < 0) return WST_ERR_INVALID_ARG;
-  if (c.flags & ~(WST_FLAG_KAHAN | WST_FLAG_FP64_SCREEN | WST_FLAG_TIMING)) return WST_ERR_INVALID_ARG;
+  if (c.flags & ~(WST_FLAG_KAHAN | WST_FLAG_FP64_SCREEN | WST_FLAG_TIMING | WST_FLAG_WFOLD))
+    return WST_ERR_INVALID_ARG;
   const int64_t n_buckets = (int64_t)c.batch * c.n_w * c.n * kColBlocks;
   if (n_buckets + 1 >= (int64_t)0xFFFFFFFFu) return WST_ERR_UNSUPPORTED;
 
@@ -249,6 +250,7 @@ wst_status wst_plan_set_workspace(wst_plan p, void *ptr, size_t bytes) {
 wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
   if (!p) return WST_ERR_INVALID_ARG;
   if (p->cfg.kernel != WST_KERNEL_TABLE) return fail(p, WST_ERR_STATE, "plan kernel is not a table");
+  if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no kernel gradient with WST_FLAG_WFOLD");
   if (!table_dev) return fail(p, WST_ERR_INVALID_ARG, "table pointer is NULL");
   WST_CUDA(p, cudaMemcpyAsync(p->ktable, table_dev, sizeof(float) * p->cfg.ktable_len,
                               cudaMemcpyDeviceToDevice, p->stream), "table copy");
@@ -263,13 +265,14 @@ wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
 // the device's address space (on GB300 the accesses cross NVLink-C2C: the kernels read
 // the inputs and write the image in place, no separate copy); pageable host memory only
 // where the device reports cudaDevAttrPageableMemoryAccess.
-static const void *device_view(const wst_plan_s *p, const void *ptr) {
+static const void *device_view(const wst_plan_s *p, const void *ptr, bool *is_host = nullptr) {
   if (!ptr) return nullptr;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
+  if (is_host) *is_host = a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
   if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
   if (a.type == cudaMemoryTypeHost) return a.devicePointer;
   int pageable = 0;
@@ -286,9 +289,10 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   p->vis_set = false;
   if (n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return fail(p, WST_ERR_INVALID_ARG, "n_vis out of range");
   if (n_vis > 0 && (!u || !v || !w || !vis)) return fail(p, WST_ERR_INVALID_ARG, "NULL visibility array");
+  bool host_vis = false;
   if (n_vis > 0) {
     const void *du = device_view(p, u), *dv = device_view(p, v), *dw = device_view(p, w);
-    const void *dvis = device_view(p, vis), *dwt = weight ? device_view(p, weight) : nullptr;
+    const void *dvis = device_view(p, vis, &host_vis), *dwt = weight ? device_view(p, weight) : nullptr;
     if (!du || !dv || !dw || !dvis || (weight && !dwt))
       return fail(p, WST_ERR_INVALID_ARG, "visibility arrays must be device or page-locked host memory");
     u = (const float *)du;
@@ -314,6 +318,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   if (L.total > p->ws_bytes) return fail(p, WST_ERR_OOM, "workspace too small for n_vis");
   Workspace &W = p->W_;
   W.keyinfo = (uint4 *)(p->ws + L.keyinfo_planes);
+  W.stash = (float4 *)(W.keyinfo + n_vis);
   W.planes = (float2 *)(p->ws + L.keyinfo_planes);
   W.records = (Record *)(p->ws + L.records);
   W.offsets = (uint32_t *)(p->ws + L.offsets);
@@ -338,7 +343,7 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   p->n_vis = n_vis;
   p->has_weight = weight != nullptr;
   WST_CUDA(p, time_begin(p, p->ev_sort, ST_SORT), "event");
-  WST_CUDA(p, sort_visibilities(p, u, v, w, (const float2 *)vis, weight), "sort");
+  WST_CUDA(p, sort_visibilities(p, u, v, w, (const float2 *)vis, weight, host_vis), "sort");
   WST_CUDA(p, time_end(p, p->ev_sort), "event");
   p->launches_sort = p->launches;
   p->vis_set = true;
@@ -416,6 +421,7 @@ wst_status wst_degrid(wst_plan p, const void *dimage, void *dvis, uint32_t flags
   if (st) return st;
   if (!dimage || (!dvis && p->n_vis > 0)) return fail(p, WST_ERR_INVALID_ARG, "NULL buffer");
   if (flags & ~WST_NO_CORRECTION) return fail(p, WST_ERR_INVALID_ARG, "unknown flags");
+  if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no adjoint with WST_FLAG_WFOLD");
   const bool correct = !(flags & WST_NO_CORRECTION);
   if (p->n_vis > 0) WST_CUDA(p, cudaMemsetAsync(dvis, 0, sizeof(float2) * p->n_vis, p->stream), "memset");
   float2 *planes = p->W_.planes;

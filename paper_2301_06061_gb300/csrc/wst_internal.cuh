@@ -78,6 +78,7 @@ struct KernelParams {
 
 struct Workspace {
   uint4 *keyinfo;      // per visibility: key, 0, xpack, ypack (aliases the plane buffer)
+  float4 *stash;       // per visibility: value, weight, after keyinfo (host inputs only)
   Record *records;     // sorted records
   uint32_t *offsets;   // bucket offsets [n_buckets + 1]
   uint32_t *cursor;    // scatter cursors (a copy of the offsets, advanced by the scatter)
@@ -259,7 +260,7 @@ cudaError_t build_plane_centres(wst_plan_s *p);
 
 // k_sort.cu
 cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
-                              const float2 *vis, const float *weight);
+                              const float2 *vis, const float *weight, bool host_inputs);
 cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, int64_t n_bound);
 int64_t scan_tmp_words(int64_t n);
 

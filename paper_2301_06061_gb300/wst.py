@@ -23,7 +23,7 @@ STATUS = {0: "WST_OK", 1: "WST_ERR_INVALID_ARG", 2: "WST_ERR_OOM", 3: "WST_ERR_C
           4: "WST_ERR_TIMEOUT", 5: "WST_ERR_UNSUPPORTED", 6: "WST_ERR_STATE"}
 
 WST_KERNEL_GAUSS, WST_KERNEL_ES, WST_KERNEL_TABLE = 0, 1, 2
-WST_FLAG_KAHAN, WST_FLAG_FP64_SCREEN, WST_FLAG_TIMING = 0x1, 0x2, 0x4
+WST_FLAG_KAHAN, WST_FLAG_FP64_SCREEN, WST_FLAG_TIMING, WST_FLAG_WFOLD = 0x1, 0x2, 0x4, 0x8
 WST_NO_CORRECTION = 0x1
 
 EXPORTED = [

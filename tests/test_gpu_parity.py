@@ -309,6 +309,34 @@ def test_pageable_or_foreign_host_tensors_rejected_by_binding(wst):
         wst._ptr(torch.zeros(4).pin_memory())  # host memory where only device memory is accepted
 
 
+@pytest.mark.parametrize("n", [256, 8192])
+def test_wfold_placement_and_image(wst, n):
+    """WST_FLAG_WFOLD: w < 0 visibilities are mirrored before placement (the w range from
+    the data becomes [min |w|, max |w|]); placement is bit-exact and the image matches the
+    oracle run on the mirrored visibilities (its real part is the unfolded dirty image's)."""
+    u, v, w, vis = make_case(n=n, n_vis=5000, seed=41 + n)
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_WFOLD)  # range from data
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    fu, fv, fw, fvis = oracle.fold_w(u, v, w, vis)
+    lo, hi = oracle.resolve_w_range(fw, 0.0, 0.0)
+    st_ = plan.stats()
+    assert st_["w_min"] == lo and st_["w_max"] == hi and lo >= 0.0
+    k = torch.empty(u.size, dtype=torch.int32, device="cuda")
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    oc = ocfg_for(cfg, lo, hi)
+    ko, io, jo, _ = oracle.locate(oc, fu, fv, fw, fvis)
+    np.testing.assert_array_equal(k.cpu().numpy(), ko)
+    np.testing.assert_array_equal(i0.cpu().numpy(), io)
+    np.testing.assert_array_equal(j0.cpu().numpy(), jo)
+    img = plan.image()
+    assert_image_parity(img[0].cpu().numpy(), oracle.image(oc, fu, fv, fw, fvis), oc)
+    unc = plan.image(flags=wst.WST_NO_CORRECTION)
+    assert rel_err(unc[0].cpu().numpy(), oracle.image(oc, fu, fv, fw, fvis, correct=False)) < TOL
+    with pytest.raises(wst.WstError):
+        plan.degrid(img)
+
+
 @pytest.mark.parametrize("kernel,W,param", [("es", 8, 2.3 * 8), ("gauss", 8, 0.925), ("table", 8, None)])
 def test_image_kernels(wst, kernel, W, param):
     n = 256

@@ -447,3 +447,54 @@ def test_kernel_grad_finite_differences():
         tm[i] -= h
         fd = (loss(tp) - loss(tm)) / (2 * h)  # exact for a loss quadratic in the table
         assert abs(fd - g[i]) < 1e-8 * max(1.0, np.abs(g).max())
+
+
+# ------------------------------------------------------------------------------------------
+# the w-folding variant (not in the paper): Hermitian mirror of the w < 0 visibilities
+# ------------------------------------------------------------------------------------------
+
+def test_fold_keeps_the_real_part_of_the_direct_transform():
+    """A mirrored visibility (-u, -v, -w, conj V) adds the complex conjugate of the original
+    term, so Re of the exact dirty image is unchanged and Im is not."""
+    N, fov = 64, 0.1
+    rng = np.random.default_rng(21)
+    u, v, w = synth.disk_uvw(400, 0.45 * N / fov, 200.0, rng)
+    vis = synth.random_visibilities(400, rng)
+    fu, fv, fw, fvis = oracle.fold_w(u, v, w, vis)
+    assert np.all(fw >= 0) and np.array_equal(np.abs(fw), np.abs(w)) and np.array_equal(fu == u, w >= 0)
+    pix = np.arange(N)
+    a, b = np.meshgrid(pix, pix)
+    d = oracle.dft_pixels(u, v, w, vis, N, fov, a.ravel(), b.ravel())
+    df = oracle.dft_pixels(fu, fv, fw, fvis, N, fov, a.ravel(), b.ravel())
+    scale = np.abs(d).max()
+    assert np.abs(df.real - d.real).max() <= 1e-12 * scale
+    assert np.abs(df.imag - d.imag).max() > 1e-3 * scale
+
+
+def test_fold_image_within_half_range_w_bound():
+    """The folded w-stacking image approximates Re of the direct transform within the same
+    per-visibility bound as the unfolded one, with the plane offsets of the folded range
+    (half the plane spacing at the same number of planes)."""
+    N, fov, n_w = 64, 0.1, 4
+    rng = np.random.default_rng(22)
+    u, v, w = synth.disk_uvw(300, 0.45 * N / fov, 200.0, rng)
+    vis = synth.random_visibilities(300, rng)
+    fu, fv, fw, fvis = oracle.fold_w(u, v, w, vis)
+    lo, hi = oracle.resolve_w_range(fw, 0.0, 0.0)
+    assert lo >= 0 and hi == float(np.abs(w).max())
+    cfg = OracleConfig(N, fov, n_w, lo, hi, 7)
+    img = oracle.image(cfg, fu, fv, fw, fvis)
+    k, _, _, st = oracle.locate(cfg, fu, fv, fw, fvis)
+    assert np.all(st == 0)
+    dwk = np.abs(fw - np.array([oracle.plane_centre(cfg, int(x)) for x in k]))
+    assert dwk.max() <= (hi - lo) / n_w / 2 * (1 + 1e-12)
+    pix = np.arange(N)
+    a, b = np.meshgrid(pix, pix)
+    d = oracle.dft_pixels(u, v, w, vis, N, fov, a.ravel(), b.ravel()).reshape(N, N)
+    dl = fov / N
+    t = np.vectorize(oracle.n_minus_one)((a - N // 2) * dl, (b - N // 2) * dl)
+    e = gauss_alias((pix - N // 2) / N, cfg.kparam, cfg.support)
+    ea = e[None, :] + e[:, None] + e[None, :] * e[:, None]
+    av = np.abs(vis).astype(np.float64)
+    bound = av.sum() * ea + (1 + ea) * np.abs(t) * 2 * np.pi * (av * dwk).sum()
+    assert np.all(np.abs(img.real - d.real) <= bound * (1 + 1e-9) + 1e-9)
