@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--snap-w", action="store_true",
                     help="place every w on its plane centre, so the error against the direct transform is "
                          "the (u,v) kernel's alone (kernel comparisons)")
+    ap.add_argument("--oversample", type=int, default=0, choices=[0, 1, 2],
+                    help="2: grid of 2N cells, the central N x N kept (images up to 8192^2)")
     ap.add_argument("--wfold", action="store_true",
                     help="mirror w < 0 visibilities (WST_FLAG_WFOLD): half the w range; the real part is the image")
     ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8"], default="gauss",
@@ -118,13 +120,14 @@ def kernel_function(kernel: str, support: int, sigma: float, table):
 
 
 def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np.ndarray,
-                 n_offsets: int = 512) -> np.ndarray:
+                 n_offsets: int = 512, oversample: int = 1) -> np.ndarray:
     """eps(a) = sup over sub-cell offsets g of |sum_taps G(t) e^{2 pi i nu t} / Ghat(nu) - 1|,
-    t = tap - W/2 + g, nu = (a - n/2)/n: the relative error of one visibility's
-    gridded, transformed and corrected contribution at pixel index a along one axis."""
+    t = tap - W/2 + g, nu = (a - n/2)/(oversample n): the relative error of one
+    visibility's gridded, transformed and corrected contribution at pixel index a along
+    one axis (an oversampled grid keeps the pixels in |nu| <= 1/(2 oversample))."""
     G, panels = kernel_function(kernel, support, sigma, table)
     half = 0.5 * support
-    nu = (idx.astype(np.float64) - n // 2) / n
+    nu = (idx.astype(np.float64) - n // 2) / (n * oversample)
     # Ghat(nu) = integral of G(t) cos(2 pi nu t) over the support: 4-point Gauss-Legendre per panel
     gx, gw = np.polynomial.legendre.leggauss(4)
     edges = np.linspace(-half, half, panels + 1)
@@ -144,7 +147,7 @@ def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np
 
 
 def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev, n_pix: int, kernel: str,
-                   support: int, sigma: float, table, wfold: bool = False):
+                   support: int, sigma: float, table, wfold: bool = False, oversample: int = 1):
     """The image against the direct transform (GPU, float-float phases) at the brightest
     sources' pixels and at seeded random pixels, with the per-pixel bound
     B = sum|V| (min(2, 2 pi dmax |n - 1|) + e_a + e_b + e_a e_b) + 1e-5 peak, dmax the
@@ -183,8 +186,8 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     mb = (pb - n // 2) * fov / n
     r2 = la * la + mb * mb
     nm1 = np.abs(r2 / (1.0 + np.sqrt(np.maximum(0.0, 1.0 - r2))))
-    ea = kernel_error(kernel, support, sigma, table, n, pa)
-    eb = kernel_error(kernel, support, sigma, table, n, pb)
+    ea = kernel_error(kernel, support, sigma, table, n, pa, oversample=oversample)
+    eb = kernel_error(kernel, support, sigma, table, n, pb, oversample=oversample)
     rel = np.minimum(2.0, 2.0 * np.pi * dmax * nm1) + ea + eb + ea * eb
     bound = sum_abs * rel + 1e-5 * peak
     central = (np.abs(pa - n // 2) < n // 8) & (np.abs(pb - n // 2) < n // 8)
@@ -264,9 +267,12 @@ class ClockSampler:
 # roofline bookkeeping
 # ------------------------------------------------------------------------------------------
 
-def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept: int, n_vis: int) -> float:
-    """Algorithmic DRAM bytes of one launch of a stage (averaged over the chunks)."""
-    S = 8.0 * n * n
+def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept: int, n_vis: int,
+                oversample: int = 1) -> float:
+    """Algorithmic DRAM bytes of one launch of a stage (averaged over the chunks); the
+    planes are (oversample n)^2, the images n^2."""
+    S_img = 8.0 * n * n
+    S = S_img * oversample * oversample
     per_chunk_planes = planes / chunks
     if stage == "sort":  # read u, v, w, V (20 B) and write the 32-byte record
         return 52.0 * n_vis
@@ -275,7 +281,7 @@ def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept
     if stage in ("rows", "cols_a"):  # read + write each plane
         return 2.0 * per_chunk_planes * S
     if stage == "cols_b":  # read each plane, write the images once
-        return per_chunk_planes * S + batch * S / chunks
+        return per_chunk_planes * S + batch * S_img / chunks
     raise ValueError(stage)
 
 
@@ -397,7 +403,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
     cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
                      flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING | (wst.WST_FLAG_WFOLD if args.wfold else 0),
-                     planes_per_chunk=args.chunk, batch=batch,
+                     planes_per_chunk=args.chunk, batch=batch, oversample=args.oversample,
                      **kcfg)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_u, h_v, h_w = pin(work.u), pin(work.v), pin(work.w)
@@ -453,7 +459,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dom = max(stages, key=stages.get)
     per_launch_ms = stages[dom] / (args.steps * launches_per_stage[dom])
     planes = batch * work.n_w
-    bytes_launch = stage_bytes(dom, work.n, planes, st["n_chunks"], batch, st["n_kept"], n_vis)
+    osf = max(1, args.oversample)
+    bytes_launch = stage_bytes(dom, work.n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf)
     peak, peak_src = load_peaks()
     achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     kernel_names = {"sort": "k_keys+k_scan+k_scatter+k_row_bounds", "grid": "k_grid_rows (gridding + row FFT)",
@@ -466,7 +473,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stages.items()},
                 "stage_frac_of_hbm": {k: round(stage_bytes(k, work.n, planes, st["n_chunks"], batch, st["n_kept"],
-                                                           n_vis) * launches_per_stage[k] /
+                                                           n_vis, osf) * launches_per_stage[k] /
                                                (v / args.steps * 1e-3) / 1e9 / peak, 4)
                                       for k, v in stages.items() if v > 0}}
 
@@ -522,14 +529,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.dft_pixels > 0 and batch == 1:
         sigma = kcfg.get("kparam", 0.0)
         acc = accuracy_block(torch, wst, work, st, d_u, d_v, d_w, d_vis, img, dev, args.dft_pixels,
-                             args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold)
+                             args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold,
+                             max(1, args.oversample))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and batch == 1:
         job_s, sample, cores, osample = time_oracle_sample(work, vis_np)
         cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
                "sample": sample}
-        if args.kernel == "gauss" and not args.snap_w and not args.wfold:  # the oracle sample's setting
+        if args.kernel == "gauss" and not args.snap_w and not args.wfold and args.oversample < 2:
             cpu["parity_vs_oracle"] = oracle_parity(torch, wst, dev, osample)
 
     clocks = clk.summary()
@@ -540,7 +548,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
                        "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w,
-                       "wfold": args.wfold, "planes_per_chunk": args.chunk or planes,
+                       "wfold": args.wfold, "oversample": max(1, args.oversample),
+                       "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},

@@ -97,6 +97,9 @@ typedef struct wst_config {
   uint32_t flags;           /* WST_FLAG_*                                              */
   int32_t planes_per_chunk; /* planes held in the workspace at once; 0 = all           */
   int32_t batch;            /* independent images sharing this geometry, >= 1          */
+  int32_t oversample;       /* 0 or 1: grid = image (the paper's design); 2: a grid of  */
+                            /* 2N cells of 1/(2 fov) wavelengths, the same pixels, the */
+                            /* image the central N x N (2N <= 16384)                   */
 } wst_config;
 
 typedef struct wst_stats {
@@ -176,15 +179,16 @@ wst_status wst_plan_set_vis(wst_plan plan, int64_t n_vis, const float *u, const 
 
 /*
  * Eq. 3: grid planes [plane_begin, plane_end) (global plane index image*N_w + k)
- * into grid_out, complex64 [(plane_end - plane_begin) x N x N], natural layout.
+ * into grid_out, complex64 [(plane_end - plane_begin) x M x M], natural layout, M the
+ * grid side (N, or 2N with oversample = 2).
  */
 wst_status wst_grid(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *grid_out);
 
 /*
  * Eq. 2 for planes [plane_begin, plane_end): transform each plane of grid_inout
  * (layout of wst_grid; overwritten) with the centred positive-exponent 2D FFT,
- * multiply by the plane's phase screen and ADD into image_inout, complex64
- * [batch x N x N].  No grid correction (see wst_correct).
+ * multiply by the plane's phase screen and ADD the central N x N into image_inout,
+ * complex64 [batch x N x N].  No grid correction (see wst_correct).
  */
 wst_status wst_fft_correct(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *grid_inout,
                            void *image_inout);
@@ -207,6 +211,7 @@ wst_status wst_image(wst_plan plan, void *image_out, uint32_t flags);
  * Adjoint of wst_image (degridding; the paper lists it as future work in its
  * conclusions): dvis_j = w_j sum_taps G G g_k[q,p], g_k the centred 2D transform
  * with the negative exponent of conj(screen_k) * C_a C_b * dimage.
+ * WST_ERR_UNSUPPORTED with WST_FLAG_WFOLD or an oversampled grid.
  * dimage: complex64 [batch x N x N]; dvis_out: complex64 [n_vis] in the caller's
  * order (0 for dropped and non-finite visibilities).
  */

@@ -19,6 +19,7 @@ from .oracle import (  # noqa: F401
     gauss_legendre,
     grid,
     image,
+    image_oversampled,
     image_pixels,
     kernel_eval,
     kernel_ft,

@@ -18,6 +18,8 @@ Every function follows a passage of arXiv:2301.06061:
 * ``kernel_ft``     -- Ghat(nu), the Fourier transform of the truncated kernel
 * ``fold_w``        -- the w-folding variant's Hermitian mirror of w < 0 visibilities
                        (not in the paper; applied to the inputs of the functions above)
+* ``image_oversampled`` -- the oversampled-grid variant (not in the paper): ``image``
+                       on a grid of 2N cells, cropped to the central N x N
 
 Pins (tests/test_oracle_*.py) tie each one to something other than itself:
 numpy/pocketfft and the textbook DFT for the FFT; closed forms for Ghat and the
@@ -25,7 +27,8 @@ screen; brute-force DFT within the analytic aliasing bound for the image;
 linearity, Hermitian symmetry and the single-visibility flat image; the
 dot-product identity for the adjoint; finite differences for the kernel
 gradient; exact integer placement rules for ``locate``; for ``fold_w``, the
-invariance of the real part of the direct transform.
+invariance of the real part of the direct transform; for ``image_oversampled``, the
+direct transform within the aliasing bound of the half-band frequencies.
 """
 from __future__ import annotations
 
@@ -261,6 +264,19 @@ def image(cfg: OracleConfig, u, v, w, vis, weight=None, correct: bool = True) ->
     _load().wo_image(cfg._c(), u.size, u.ctypes.data, v.ctypes.data, w.ctypes.data,
                      visf.ctypes.data, _ptr(wt), int(bool(correct)), out.ctypes.data)
     return out
+
+
+def image_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, weight=None,
+                      correct: bool = True) -> np.ndarray:
+    """The oversampled-grid variant (not in the paper): the image of ``cfg`` (N pixels of
+    fov/N) as the central N x N of the plain algorithm run on a grid of oversample * N
+    cells of 1/(oversample * fov) wavelengths -- the same pixels, a wider transform."""
+    n = cfg.n
+    big = OracleConfig(n * oversample, cfg.fov * oversample, cfg.n_w, cfg.w_min, cfg.w_max, cfg.support,
+                       cfg.kernel, cfg.kparam, cfg.ktable)
+    full = image(big, u, v, w, vis, weight, correct)
+    c = (n * oversample - n) // 2
+    return full[c:c + n, c:c + n].copy()
 
 
 def image_pixels(cfg: OracleConfig, u, v, w, vis, pa, pb, weight=None,

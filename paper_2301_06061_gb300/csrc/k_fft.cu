@@ -501,7 +501,8 @@ __device__ __forceinline__ void flush_pixel(float2 *im, float2 *cp, size_t o, fl
 template <int LA, bool FP64S>
 __global__ void __launch_bounds__(ColCfg<LA>::THREADS, ColCfg<LA>::THREADS >= 32 ? 512 / ColCfg<LA>::THREADS : 1)
 k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
-             int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
+             int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags,
+             int n_img, int crop) {
   using C = ColCfg<LA>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LA, EPT);
@@ -514,7 +515,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int col0 = blockIdx.x * kCB;
+  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
   const int kp = col0 + col;
   auto smi = [col](int i) { return i * C::PADW + col; };
   const bool kahan = flags & ACC_KAHAN;
@@ -589,39 +590,17 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
     // or after p0, and is complete if its last plane is before p1
     const bool first_any = img * n_w >= p0;
     const bool last_any = (img + 1) * n_w <= p1;
-    float2 *im = image + (size_t)img * n * n;
-    float2 *cp = comp ? comp + (size_t)img * n * n : nullptr;
+    float2 *im = image + (size_t)img * n_img * n_img;
+    float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         const int e = b * RL + r;
         const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-        const size_t o = (size_t)kq * n + kp;
-        float2 sum = s[e], cmp = cc[e];
-        if (flags & ACC_STAGED) {
-          im[o] = cadd(im[o], csub(sum, cmp));
-          continue;
-        }
-        if (!first_any) {  // merge with the running (sum, compensation) of earlier chunks
-          float2 acc_s = im[o];
-          float2 acc_c = cp ? cp[o] : make_float2(0.0f, 0.0f);
-          kahan_add(acc_s, acc_c, sum);
-          kahan_add(acc_s, acc_c, make_float2(-cmp.x, -cmp.y));
-          sum = acc_s;
-          cmp = acc_c;
-        }
-        if (last_any) {
-          float2 out = csub(sum, cmp);
-          if (flags & ACC_CORRECT) {
-            const float f = sc.corr[kp] * sc.corr[kq];
-            out = make_float2(out.x * f, out.y * f);
-          }
-          im[o] = out;
-        } else {
-          im[o] = sum;
-          if (cp) cp[o] = cmp;
-        }
+        if (kq < crop || kq >= crop + n_img) continue;  // a grid row outside the image
+        const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
+        flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
   }
 }
@@ -633,7 +612,8 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
 template <int LA, bool FP64S>
 __global__ void __launch_bounds__(LA / 16 * kCB, LA == 128 ? 3 : 6)
 k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
-           int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags) {
+           int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags,
+           int n_img, int crop) {
   constexpr int EPT = 16, TPL = LA / EPT, THREADS = TPL * kCB, R1 = LA / 16;
   static_assert(num_stages(LA, EPT) == 2 && stage_radix(LA, EPT, 1) == R1, "two stages");
   __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
@@ -643,7 +623,7 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int col0 = blockIdx.x * kCB;
+  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
   const int kp = col0 + col;
   const bool kahan = flags & ACC_KAHAN;
   const size_t plane_elems = (size_t)n * n;
@@ -736,16 +716,17 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
     }
     const bool first_any = img * n_w >= p0;
     const bool last_any = (img + 1) * n_w <= p1;
-    float2 *im = image + (size_t)img * n * n;
-    float2 *cp = comp ? comp + (size_t)img * n * n : nullptr;
+    float2 *im = image + (size_t)img * n_img * n_img;
+    float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
     for (int b = 0; b < EPT / R1; ++b)
 #pragma unroll
       for (int r = 0; r < R1; ++r) {
         const int e = b * R1 + r;
         const int kq = out_row(b, r);
+        if (kq < crop || kq >= crop + n_img) continue;  // a grid row outside the image
         const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
-        flush_pixel(im, cp, (size_t)kq * n + kp, s[e], cc[e], first_any, last_any, flags, f);
+        flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
   }
 }
@@ -820,12 +801,12 @@ k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, Tw tw,
 }
 
 // elementwise grid correction
-__global__ void k_correct(float2 *image, const float *corr, int n, int64_t total) {
+__global__ void k_correct(float2 *image, const float *corr, int n, int crop, int64_t total) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pix = i % ((int64_t)n * n);
     const int a = (int)(pix % n), b = (int)(pix / n);
-    const float f = corr[a] * corr[b];
+    const float f = corr[a + crop] * corr[b + crop];  // corr is indexed on the grid
     float2 x = image[i];
     image[i] = make_float2(x.x * f, x.y * f);
   }
@@ -952,23 +933,25 @@ static bool fp64_screen(const wst_plan_s *p) { return (p->cfg.flags & WST_FLAG_F
 template <int LA>
 static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                  float2 *comp, int flags) {
-  dim3 grd(p->n / kCB, p->n / LA);
+  dim3 grd(p->n_img / kCB, p->n / LA);  // the image's column bands of the grid, every row block
   if constexpr (LA == 64 || LA == 128) {
     constexpr int THREADS = LA / 16 * kCB;
     if (fp64_screen(p))
       k_cols_b16<LA, true><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
-                                                           image, comp, flags);
+                                                           image, comp, flags, p->n_img, p->crop);
     else
       k_cols_b16<LA, false><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
-                                                            image, comp, flags);
+                                                            image, comp, flags, p->n_img, p->crop);
     return cudaGetLastError();
   }
   if (fp64_screen(p))
     k_cols_b_acc<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                        screen_ctx(p), image, comp, flags);
+                                                                        screen_ctx(p), image, comp, flags, p->n_img,
+                                                                        p->crop);
   else
     k_cols_b_acc<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                         screen_ctx(p), image, comp, flags);
+                                                                         screen_ctx(p), image, comp, flags, p->n_img,
+                                                                         p->crop);
   return cudaGetLastError();
 }
 
@@ -1018,10 +1001,10 @@ cudaError_t fft_cols_bh_from_image(wst_plan_s *p, const float2 *dimage, int p0, 
 }
 
 cudaError_t correct_image(wst_plan_s *p, float2 *image) {
-  const int64_t total = (int64_t)p->batch * p->n * p->n;
+  const int64_t total = (int64_t)p->batch * p->n_img * p->n_img;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_correct<<<(unsigned)blocks, 256, 0, p->stream>>>(image, p->corr, p->n, total);
+  k_correct<<<(unsigned)blocks, 256, 0, p->stream>>>(image, p->corr, p->n_img, p->crop, total);
   p->launches += 1;
   return cudaGetLastError();
 }

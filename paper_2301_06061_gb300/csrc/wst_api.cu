@@ -72,7 +72,7 @@ Layout layout_for(const wst_plan_s *p, int64_t n_vis) {
   L.rowbound = off;
   if (p->n >= kFixedMinN) off += align_up((size_t)(p->n_buckets / kColBlocks) * sizeof(float2));
   L.comp = off;
-  if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n * p->n * sizeof(float2));
+  if (p->chunk < p->n_planes) off += align_up((size_t)p->batch * p->n_img * p->n_img * sizeof(float2));
   L.total = off;
   return L;
 }
@@ -150,8 +150,16 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   if (!out) return WST_ERR_INVALID_ARG;
   *out = nullptr;
   if (!cfg) return WST_ERR_INVALID_ARG;
-  const wst_config c = *cfg;
-  if (!is_pow2(c.n) || c.n < 64 || c.n > 16384) return WST_ERR_UNSUPPORTED;
+  if (cfg->oversample < 0 || cfg->oversample > 2) return WST_ERR_UNSUPPORTED;
+  const int os = cfg->oversample == 2 ? 2 : 1;
+  // the plan works on the grid: os N cells of 1/(os fov) (the same pixel size), and
+  // images are the central N x N of the grid's transform
+  wst_config c = *cfg;
+  if (!is_pow2(cfg->n) || cfg->n < 64) return WST_ERR_UNSUPPORTED;
+  c.n = cfg->n * os;
+  c.fov = cfg->fov * os;
+  c.oversample = os;
+  if (c.n > 16384) return WST_ERR_UNSUPPORTED;
   if (!(c.fov > 0.0) || !isfinite(c.fov)) return WST_ERR_INVALID_ARG;
   if (c.n_w < 1 || c.n_w > 4096) return WST_ERR_INVALID_ARG;
   if (!isfinite(c.w_min) || !isfinite(c.w_max) || c.w_min > c.w_max) return WST_ERR_INVALID_ARG;
@@ -174,6 +182,8 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   p->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&p->device);
   p->n = c.n;
+  p->n_img = cfg->n;
+  p->crop = (c.n - cfg->n) / 2;
   p->log2n = ilog2(c.n);
   p->W = c.support;
   p->n_w = c.n_w;
@@ -251,6 +261,7 @@ wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
   if (!p) return WST_ERR_INVALID_ARG;
   if (p->cfg.kernel != WST_KERNEL_TABLE) return fail(p, WST_ERR_STATE, "plan kernel is not a table");
   if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no kernel gradient with WST_FLAG_WFOLD");
+  if (p->crop) return fail(p, WST_ERR_UNSUPPORTED, "no kernel gradient with an oversampled grid");
   if (!table_dev) return fail(p, WST_ERR_INVALID_ARG, "table pointer is NULL");
   WST_CUDA(p, cudaMemcpyAsync(p->ktable, table_dev, sizeof(float) * p->cfg.ktable_len,
                               cudaMemcpyDeviceToDevice, p->stream), "table copy");
@@ -422,6 +433,7 @@ wst_status wst_degrid(wst_plan p, const void *dimage, void *dvis, uint32_t flags
   if (!dimage || (!dvis && p->n_vis > 0)) return fail(p, WST_ERR_INVALID_ARG, "NULL buffer");
   if (flags & ~WST_NO_CORRECTION) return fail(p, WST_ERR_INVALID_ARG, "unknown flags");
   if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no adjoint with WST_FLAG_WFOLD");
+  if (p->crop) return fail(p, WST_ERR_UNSUPPORTED, "no adjoint with an oversampled grid");
   const bool correct = !(flags & WST_NO_CORRECTION);
   if (p->n_vis > 0) WST_CUDA(p, cudaMemsetAsync(dvis, 0, sizeof(float2) * p->n_vis, p->stream), "memset");
   float2 *planes = p->W_.planes;

@@ -101,6 +101,9 @@ struct wst_plan_s {
   int device = 0;
   // geometry
   int n = 0, log2n = 0, W = 0, n_w = 0, batch = 1, n_planes = 0, chunk = 0;
+  // oversampled grid: the kernels work on the grid (n, cfg.fov of the grid); the image
+  // is the central n_img x n_img of it, starting at grid index crop
+  int n_img = 0, crop = 0;
   int fa = 0, fb = 0;  // four-step column split N = fa * fb (fa contiguous block rows)
   int64_t n_buckets = 0;
   // owned device tables

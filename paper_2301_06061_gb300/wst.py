@@ -55,6 +55,7 @@ class wst_config(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("planes_per_chunk", ctypes.c_int32),
         ("batch", ctypes.c_int32),
+        ("oversample", ctypes.c_int32),
     ]
 
 
@@ -296,10 +297,12 @@ class Config:
     flags: int = WST_FLAG_KAHAN
     planes_per_chunk: int = 0
     batch: int = 1
+    oversample: int = 0
 
     def c(self) -> wst_config:
         return wst_config(self.n, self.fov, self.n_w, self.w_min, self.w_max, self.support, self.kernel,
-                          self.kparam, self.ktable_len, self.flags, self.planes_per_chunk, self.batch)
+                          self.kparam, self.ktable_len, self.flags, self.planes_per_chunk, self.batch,
+                          self.oversample)
 
 
 DEFAULT_SIGMA = {7: 0.875, 8: 0.925}

@@ -337,6 +337,45 @@ def test_wfold_placement_and_image(wst, n):
         plan.degrid(img)
 
 
+@pytest.mark.parametrize("n,chunk", [(256, 0), (256, 2), (4096, 0)])
+def test_oversampled_grid_image(wst, n, chunk):
+    """oversample = 2: a 2N grid of 1/(2 fov) cells and the central N x N of its transform
+    (the same pixels); the image matches the oracle's oversampled image (whole image at
+    1e-5 of the peak: no corner amplification, the correction stays within the half
+    band), also with the planes in chunks (Kahan merge into an N x N image)."""
+    u, v, w, vis = make_case(n=n, n_vis=4000, seed=51 + n + chunk)
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0, oversample=2, planes_per_chunk=chunk)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    img = plan.image()
+    assert img.shape == (1, n, n)
+    oc = ocfg_for(cfg, -200.0, 200.0)
+    ref = oracle.image_oversampled(oc, 2, u, v, w, vis)
+    assert rel_err(img[0].cpu().numpy(), ref) < TOL
+    unc = plan.image(flags=wst.WST_NO_CORRECTION)
+    assert rel_err(unc[0].cpu().numpy(), oracle.image_oversampled(oc, 2, u, v, w, vis, correct=False)) < TOL
+    with pytest.raises(wst.WstError):
+        plan.degrid(img)
+
+
+def test_oversampled_grid_staged_path(wst):
+    """wst_grid returns the 2N x 2N planes; wst_fft_correct adds the central N x N of their
+    screened transforms and wst_correct applies the grid's correction to it."""
+    n = 256
+    u, v, w, vis = make_case(n=n, n_vis=3000, seed=57)
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0, oversample=2)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    g = torch.empty((3, 2 * n, 2 * n), dtype=torch.complex64, device="cuda")
+    wst.wst_grid(plan.handle, 0, 3, g)
+    oc = ocfg_for(cfg, -200.0, 200.0)
+    big = OracleConfig(2 * n, 0.2, 3, -200.0, 200.0, oc.support, oc.kernel, oc.kparam)
+    assert rel_err(g.cpu().numpy(), oracle.grid(big, u, v, w, vis)) < TOL
+    img = torch.zeros((1, n, n), dtype=torch.complex64, device="cuda")
+    wst.wst_fft_correct(plan.handle, 0, 3, g, img)
+    assert rel_err(img[0].cpu().numpy(), oracle.image_oversampled(oc, 2, u, v, w, vis, correct=False)) < TOL
+    wst.wst_correct(plan.handle, img)
+    assert rel_err(img[0].cpu().numpy(), oracle.image_oversampled(oc, 2, u, v, w, vis)) < TOL
+
+
 @pytest.mark.parametrize("kernel,W,param", [("es", 8, 2.3 * 8), ("gauss", 8, 0.925), ("table", 8, None)])
 def test_image_kernels(wst, kernel, W, param):
     n = 256

@@ -498,3 +498,27 @@ def test_fold_image_within_half_range_w_bound():
     av = np.abs(vis).astype(np.float64)
     bound = av.sum() * ea + (1 + ea) * np.abs(t) * 2 * np.pi * (av * dwk).sum()
     assert np.all(np.abs(img.real - d.real) <= bound * (1 + 1e-9) + 1e-9)
+
+
+# ------------------------------------------------------------------------------------------
+# the oversampled-grid variant (not in the paper): a 2N grid, the central N x N kept
+# ------------------------------------------------------------------------------------------
+
+def test_oversampled_image_within_half_band_aliasing_bound():
+    """w snapped to plane centres: the oversampled image's pixels are the grid's central
+    half, |nu| <= 1/4 on the 2N grid, so the aliasing bound sum|V| (e_a + e_b + e_a e_b)
+    with e taken there holds over the WHOLE image, and is small everywhere -- where the
+    plain grid's edge pixels alias by design."""
+    cfg, u, v, w, vis = _snapped_case()
+    N = cfg.n
+    img = oracle.image_oversampled(cfg, 2, u, v, w, vis)
+    a, b = np.meshgrid(np.arange(N), np.arange(N))
+    d = oracle.dft_pixels(u, v, w, vis, N, cfg.fov, a.ravel(), b.ravel()).reshape(N, N)
+    nu = (np.arange(N) + N // 2 - N) / (2 * N)  # grid index a + N/2 on the 2N grid
+    assert np.abs(nu).max() <= 0.25
+    e = gauss_alias(nu, cfg.kparam, cfg.support)
+    bound = np.abs(vis).astype(np.float64).sum() * (e[None, :] + e[:, None] + e[None, :] * e[:, None])
+    err = np.abs(img - d)
+    assert np.all(err <= bound * (1 + 1e-9) + 1e-9)
+    plain = np.abs(oracle.image(cfg, u, v, w, vis) - d)
+    assert err.max() < 2e-3 * np.abs(d).max() and err.max() * 20 < plain.max()
