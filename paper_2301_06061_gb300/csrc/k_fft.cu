@@ -419,20 +419,17 @@ __device__ __forceinline__ void kahan_add(float2 &s, float2 &c, float2 y) {
   s.y = ty;
 }
 
-// float-float screen from a cached t = n - 1 (t.x is NaN outside the unit sphere)
+// float-float screen of the plane at w from a cached t = n - 1 (t.x is NaN outside the
+// unit sphere), and (STEP) the step for the plane spacing dw
 template <bool STEP>
-__device__ __forceinline__ void screen_from_t(const ScreenCtx &sc, float2 t2, int P, int img, float scale,
-                                              float2 &scr, float2 &stp) {
+__device__ __forceinline__ void screen_from_t(float2 t2, float2 w, float2 dw, float scale, float2 &scr,
+                                              float2 &stp) {
   scr = make_float2(0.0f, 0.0f);
   if (STEP) stp = make_float2(0.0f, 0.0f);
   if (isnan(t2.x)) return;
   const ff t = {t2.x, t2.y};
-  const float2 w = sc.wc[P];
   scr = cis_cycles_ff(ff_mul({w.x, w.y}, t));
-  if (STEP) {
-    const float2 dw = sc.dwff[img];
-    stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
-  }
+  if (STEP) stp = cis_cycles_ff(ff_mul({dw.x, dw.y}, t));
   scr.x *= scale;
   scr.y *= scale;
 }
@@ -498,11 +495,15 @@ __device__ __forceinline__ void flush_pixel(float2 *im, float2 *cp, size_t o, fl
   }
 }
 
-template <int LA, bool FP64S>
+template <int LA, bool FP64S, bool CROP>
 __global__ void __launch_bounds__(ColCfg<LA>::THREADS, ColCfg<LA>::THREADS >= 32 ? 512 / ColCfg<LA>::THREADS : 1)
 k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
              int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags,
-             int n_img, int crop) {
+             int n_img_arg, int crop_arg) {
+  // an image smaller than the grid (CROP) is its central n_img x n_img from grid index
+  // crop; otherwise both are compile-time facts, which keeps the registers of the
+  // plain kernel free for the transform
+  const int n_img = CROP ? n_img_arg : n, crop = CROP ? crop_arg : 0;
   using C = ColCfg<LA>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LA, EPT);
@@ -559,9 +560,9 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
                 bool valid;
                 const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
                 t2 = valid ? make_float2(t.hi, t.lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
-                screen_from_t<true>(sc, t2, P, img, sg, scr[b * RL + r], st);
+                screen_from_t<true>(t2, sc.wc[P], sc.dwff[img], sg, scr[b * RL + r], st);
               } else {
-                screen_from_t<false>(sc, t2, P, img, sg, scr[b * RL + r], st);
+                screen_from_t<false>(t2, sc.wc[P], sc.dwff[img], sg, scr[b * RL + r], st);
               }
             }
           }
@@ -598,7 +599,7 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       for (int r = 0; r < RL; ++r) {
         const int e = b * RL + r;
         const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-        if (kq < crop || kq >= crop + n_img) continue;  // a grid row outside the image
+        if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
         const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
         flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
@@ -609,11 +610,12 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
 // one exchange per plane, made in place in the plane's staging buffer (each half-warp
 // covers the 16 columns at one line position), so a plane costs four barriers for 16
 // outputs per thread.  Screen, Kahan sum and flush as in k_cols_b_acc.
-template <int LA, bool FP64S>
+template <int LA, bool FP64S, bool CROP>
 __global__ void __launch_bounds__(LA / 16 * kCB, LA == 128 ? 3 : 6)
 k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
            int n, ScreenCtx sc, float2 *__restrict__ image, float2 *__restrict__ comp, int flags,
-           int n_img, int crop) {
+           int n_img_arg, int crop_arg) {
+  const int n_img = CROP ? n_img_arg : n, crop = CROP ? crop_arg : 0;  // as in k_cols_b_acc
   constexpr int EPT = 16, TPL = LA / EPT, THREADS = TPL * kCB, R1 = LA / 16;
   static_assert(num_stages(LA, EPT) == 2 && stage_radix(LA, EPT, 1) == R1, "two stages");
   __shared__ __align__(16) float2 stage_buf[2][LA * kCB];
@@ -654,6 +656,8 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
         // live at a time; the results pass through the free staging buffer (the one the
         // next plane's tile goes to), before that copy is issued
         float2 *s_anchor = stage_buf[(P + 1 - p0) & 1];
+        const float2 wP = FP64S ? make_float2(0.0f, 0.0f) : sc.wc[P];
+        const float2 dwI = FP64S ? make_float2(0.0f, 0.0f) : sc.dwff[img];
 #pragma unroll 1
         for (int e = 0; e < EPT; ++e) {
           const int kq = out_row(e / R1, e % R1);
@@ -669,9 +673,9 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
               bool valid;
               const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
               t2 = valid ? make_float2(t.hi, t.lo) : make_float2(__int_as_float(0x7fc00000), 0.0f);
-              screen_from_t<true>(sc, t2, P, img, sg, a, st);
+              screen_from_t<true>(t2, wP, dwI, sg, a, st);
             } else {
-              screen_from_t<false>(sc, t2, P, img, sg, a, st);
+              screen_from_t<false>(t2, wP, dwI, sg, a, st);
             }
           }
           s_anchor[e * THREADS + threadIdx.x] = a;
@@ -724,7 +728,7 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       for (int r = 0; r < R1; ++r) {
         const int e = b * R1 + r;
         const int kq = out_row(b, r);
-        if (kq < crop || kq >= crop + n_img) continue;  // a grid row outside the image
+        if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
         const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
         flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
@@ -930,28 +934,26 @@ static ScreenCtx screen_ctx(wst_plan_s *p) {
 
 static bool fp64_screen(const wst_plan_s *p) { return (p->cfg.flags & WST_FLAG_FP64_SCREEN) != 0; }
 
+template <int LA, bool FP64S, bool CROP>
+static void launch_cols_b_variant(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
+                                  float2 *comp, int flags) {
+  dim3 grd(p->n_img / kCB, p->n / LA);  // the image's column bands of the grid, every row block
+  if constexpr (LA == 64 || LA == 128)
+    k_cols_b16<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
+        planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
+  else
+    k_cols_b_acc<LA, FP64S, CROP><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(
+        planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
+}
+
 template <int LA>
 static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                  float2 *comp, int flags) {
-  dim3 grd(p->n_img / kCB, p->n / LA);  // the image's column bands of the grid, every row block
-  if constexpr (LA == 64 || LA == 128) {
-    constexpr int THREADS = LA / 16 * kCB;
-    if (fp64_screen(p))
-      k_cols_b16<LA, true><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
-                                                           image, comp, flags, p->n_img, p->crop);
-    else
-      k_cols_b16<LA, false><<<grd, THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p),
-                                                            image, comp, flags, p->n_img, p->crop);
-    return cudaGetLastError();
-  }
-  if (fp64_screen(p))
-    k_cols_b_acc<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                        screen_ctx(p), image, comp, flags, p->n_img,
-                                                                        p->crop);
-  else
-    k_cols_b_acc<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(planes, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                         screen_ctx(p), image, comp, flags, p->n_img,
-                                                                         p->crop);
+  const bool fp64 = fp64_screen(p), crop = p->crop != 0;
+  if (fp64 && crop) launch_cols_b_variant<LA, true, true>(p, planes, p0, p1, image, comp, flags);
+  else if (fp64) launch_cols_b_variant<LA, true, false>(p, planes, p0, p1, image, comp, flags);
+  else if (crop) launch_cols_b_variant<LA, false, true>(p, planes, p0, p1, image, comp, flags);
+  else launch_cols_b_variant<LA, false, false>(p, planes, p0, p1, image, comp, flags);
   return cudaGetLastError();
 }
 

@@ -176,34 +176,28 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
   return quick_two_sum(p.hi, e);
 }
-__device__ __forceinline__ ff ff_sqrt(ff x) {  // x.hi > 0
-  float s = __fsqrt_rn(x.hi);
-  ff p = two_prod(s, s);
-  float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
-  return quick_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
-}
-__device__ __forceinline__ ff ff_div(ff x, ff y) {
-  float q1 = __fdiv_rn(x.hi, y.hi);
-  ff p = ff_mul({q1, 0.0f}, y);
-  ff r = ff_add(x, ff_neg(p));
-  float q2 = __fdiv_rn(r.hi, y.hi);
-  return quick_two_sum(q1, q2);
-}
 __host__ __device__ __forceinline__ float2 ff_split(double d) {
   float hi = (float)d;
   float lo = (float)(d - (double)hi);
   return make_float2(hi, lo);
 }
 
-// n - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)) in float-float; valid = l^2+m^2 < 1
+// n - 1 = sqrt(1 - l^2 - m^2) - 1 in float-float; valid = l^2 + m^2 < 1.  Only the
+// absolute error of n - 1 reaches the phase w (n - 1), so the root is taken without a
+// division: s0 = x rsqrt(x) (relative error ~2^-22), then one Newton step
+// s = s0 + (x - s0^2) rsqrt(x) / 2 with the residual formed exactly (two_prod), which
+// leaves a relative error near 2^-44; s - 1 is then an error-free float-float sum.
 __device__ __forceinline__ ff n_minus_one_ff(float2 l2, float2 m2, bool &valid) {
   ff r2 = ff_add({l2.x, l2.y}, {m2.x, m2.y});
   valid = r2.hi < 1.0f;
   if (!valid) return {0.0f, 0.0f};
-  ff om = ff_add({1.0f, 0.0f}, ff_neg(r2));
-  ff s = ff_sqrt(om);
-  ff den = ff_add({1.0f, 0.0f}, s);
-  return ff_neg(ff_div(r2, den));
+  const ff x = ff_add({1.0f, 0.0f}, ff_neg(r2));  // x.hi >= 2^-24 > 0
+  const float rs = rsqrtf(x.hi);
+  const float s0 = __fmul_rn(x.hi, rs);
+  const ff p = two_prod(s0, s0);
+  const float res = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
+  const ff s = quick_two_sum(s0, __fmul_rn(res, __fmul_rn(0.5f, rs)));
+  return ff_add(s, {-1.0f, 0.0f});
 }
 
 // exp(2 pi i phi) for a float-float phase in cycles: reduce modulo one cycle exactly
