@@ -192,7 +192,7 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     bound = sum_abs * rel + 1e-5 * peak
     central = (np.abs(pa - n // 2) < n // 8) & (np.abs(pb - n // 2) < n // 8)
     inner = (np.abs(pa - n // 2) < 3 * n // 8) & (np.abs(pb - n // 2) < 3 * n // 8)  # central 3/4
-    return {"judge": "wst_dft (GPU direct transform of Eq. 2 with float-float phases)",
+    return {"reference": "wst_dft (GPU direct transform of Eq. 2 with float-float phases)",
             "sky": f"{sky.flux.size} point sources, visibilities by Eq. 1 (wst_predict_points)",
             "pixels": int(pa.size), "source_pixels": int(sa.size),
             "max_err_rel_peak": float(err.max() / peak),

@@ -58,7 +58,7 @@ typedef enum wst_status {
   WST_ERR_OOM = 2,         /* a table allocation failed or the workspace is short  */
   WST_ERR_CUDA = 3,        /* a CUDA runtime call failed (see wst_last_error)      */
   WST_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out                   */
-  WST_ERR_UNSUPPORTED = 5, /* valid but outside what this build implements         */
+  WST_ERR_UNSUPPORTED = 5, /* valid but outside what this library implements       */
   WST_ERR_STATE = 6        /* call out of order (e.g. no visibilities set)         */
 } wst_status;
 

@@ -1,5 +1,5 @@
 """GPU parity of the adjoint (degridding), the autograd binding, the tabulated-kernel
-gradient and the direct-transform judge, against the FP64 oracle."""
+gradient and the direct transform (the accuracy reference), against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -136,7 +136,7 @@ def test_kernel_grad_matches_oracle(wst, n):
     assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()
 
 
-def test_dft_judge_matches_oracle(wst):
+def test_dft_matches_oracle(wst):
     n, fov = 512, 0.3
     rng = np.random.default_rng(12)
     u, v, w = synth.disk_uvw(20000, 0.45 * n / fov, 3000.0, rng)

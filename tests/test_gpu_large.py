@@ -77,7 +77,7 @@ def test_16k_geometry_sampled(wst):
 
 def test_full_benchmark_workload_sampled(wst):
     """The benchmark's workload (1e8 visibilities, 32 planes, all planes resident) and its
-    launch configuration, checked at 24 pixels; the GPU direct-transform judge is checked
+    launch configuration, checked at 24 pixels; the GPU direct transform is checked
     against the oracle's direct transform at the same pixels."""
     work = synth.large()
     vis = synth.random_visibilities(work.n_vis, synth.rng_for(3, 7))
@@ -94,8 +94,8 @@ def test_full_benchmark_workload_sampled(wst):
     img_u = plan.image(flags=wst.WST_NO_CORRECTION)[0]
     got_u = img_u[dev(pb).long(), dev(pa).long()].cpu().numpy()
     del img_u
-    judge = torch.empty(pa.size, dtype=torch.complex64, device="cuda")
-    wst.wst_dft(du, dv, dw, dvis, n, work.fov, dev(pa), dev(pb), judge)
+    dft_out = torch.empty(pa.size, dtype=torch.complex64, device="cuda")
+    wst.wst_dft(du, dv, dw, dvis, n, work.fov, dev(pa), dev(pb), dft_out)
     st = plan.stats()
     assert st["n_kept"] == work.n_vis and st["device_error"] == 0
     lo, hi = oracle.resolve_w_range(work.w, 0.0, 0.0)
@@ -103,4 +103,4 @@ def test_full_benchmark_workload_sampled(wst):
     ref_u = oracle.image_pixels(ocfg, work.u, work.v, work.w, vis, pa, pb, correct=False)
     check_sampled(got_c, got_u, corrected(ocfg, ref_u, pa, pb), ref_u, pa, pb, n)
     ref_dft = oracle.dft_pixels(work.u, work.v, work.w, vis, n, work.fov, pa, pb)
-    assert np.abs(judge.cpu().numpy() - ref_dft).max() <= TOL * np.abs(ref_dft).max()
+    assert np.abs(dft_out.cpu().numpy() - ref_dft).max() <= TOL * np.abs(ref_dft).max()
