@@ -13,6 +13,7 @@ from .oracle import (  # noqa: F401
     build,
     degrid,
     dft_pixels,
+    expand_rows,
     fft1d,
     fft2_centered,
     fold_w,

@@ -20,6 +20,9 @@ Every function follows a passage of arXiv:2301.06061:
                        (not in the paper; applied to the inputs of the functions above)
 * ``image_oversampled`` -- the oversampled-grid variant (not in the paper): ``image``
                        on a grid of 2N cells, cropped to the central N x N
+* ``expand_rows``   -- per-visibility (u, v, w) in wavelengths from per-row baseline
+                       coordinates in metres and per-channel nu / c (the layout of
+                       the LOFAR datasets of section 4; input expansion only)
 
 Pins (tests/test_oracle_*.py) tie each one to something other than itself:
 numpy/pocketfft and the textbook DFT for the FFT; closed forms for Ghat and the
@@ -28,7 +31,10 @@ linearity, Hermitian symmetry and the single-visibility flat image; the
 dot-product identity for the adjoint; finite differences for the kernel
 gradient; exact integer placement rules for ``locate``; for ``fold_w``, the
 invariance of the real part of the direct transform; for ``image_oversampled``, the
-direct transform within the aliasing bound of the half-band frequencies.
+direct transform within the aliasing bound of the half-band frequencies; for
+``expand_rows``, exactly representable products, the (row, channel) order with a
+partial last row, and a product whose one rounding differs from rounding its factors
+first.
 """
 from __future__ import annotations
 
@@ -157,6 +163,20 @@ def fold_w(u, v, w, vis):
     u[m], v[m], w[m] = -u[m], -v[m], -w[m]
     vis[m] = np.conj(vis[m])
     return u, v, w, vis
+
+
+def expand_rows(uvw_m, chan_scale, n_vis: int):
+    """Coordinates of visibilities stored by row (one baseline at one time) and channel,
+    as in the LOFAR datasets of section 4: visibility i is row i // C, channel i % C
+    (C channels), at (u, v, w) = baseline (metres) x nu_c / c in wavelengths, the
+    product taken in FP64 and rounded once to FP32."""
+    uvw_m = np.asarray(uvw_m, dtype=np.float64).reshape(-1, 3)
+    scale = np.asarray(chan_scale, dtype=np.float64).reshape(-1)
+    if n_vis > uvw_m.shape[0] * scale.size:
+        raise ValueError("n_vis exceeds rows x channels")
+    i = np.arange(int(n_vis))
+    row, ch = i // scale.size, i % scale.size
+    return tuple((uvw_m[row, k] * scale[ch]).astype(np.float32) for k in range(3))
 
 
 def resolve_w_range(w: np.ndarray, w_min: float, w_max: float) -> tuple[float, float]:

@@ -82,6 +82,18 @@ def earth_rotation_uvw(bl_xyz: np.ndarray, dec_deg: float, hour_angles_rad: np.n
     return np.stack([u, v, w], axis=-1)
 
 
+def array_rows(n_stations: int, diameter_m: float, n_dumps: int, freqs_hz: np.ndarray,
+               rng: np.random.Generator, lat_deg: float = 52.9, dec_deg: float = 45.0,
+               track_hours: float = 8.0):
+    """Earth-rotation tracks by row: FP64 [n_dumps * n_baselines, 3] baseline coordinates
+    in metres, ordered (time, baseline), and FP64 [n_chan] channel scales nu / c."""
+    enu = station_layout(n_stations, diameter_m, rng)
+    bl = baselines_xyz(enu, lat_deg)
+    ha = np.linspace(-0.5, 0.5, n_dumps) * track_hours * (2.0 * np.pi / 24.0)
+    uvw_m = earth_rotation_uvw(bl, dec_deg, ha).reshape(-1, 3)
+    return np.ascontiguousarray(uvw_m, dtype=np.float64), np.asarray(freqs_hz, dtype=np.float64) / C_LIGHT
+
+
 def array_uvw(n_stations: int, diameter_m: float, n_dumps: int, freqs_hz: np.ndarray,
               rng: np.random.Generator, lat_deg: float = 52.9, dec_deg: float = 45.0,
               track_hours: float = 8.0, n_vis: int | None = None):
@@ -89,16 +101,18 @@ def array_uvw(n_stations: int, diameter_m: float, n_dumps: int, freqs_hz: np.nda
 
     Returns float32 u, v, w in wavelengths, truncated to ``n_vis`` if given.
     """
-    enu = station_layout(n_stations, diameter_m, rng)
-    bl = baselines_xyz(enu, lat_deg)
-    ha = np.linspace(-0.5, 0.5, n_dumps) * track_hours * (2.0 * np.pi / 24.0)
-    uvw_m = earth_rotation_uvw(bl, dec_deg, ha).reshape(-1, 3)
-    total = uvw_m.shape[0] * len(freqs_hz)
+    uvw_m, scale = array_rows(n_stations, diameter_m, n_dumps, freqs_hz, rng, lat_deg, dec_deg, track_hours)
+    return expand_tracks(uvw_m, scale, n_vis)
+
+
+def expand_tracks(uvw_m: np.ndarray, scale: np.ndarray, n_vis: int | None = None):
+    """float32 u, v, w in wavelengths of the rows x channels, truncated to ``n_vis``."""
+    total = uvw_m.shape[0] * len(scale)
     n_vis = total if n_vis is None else min(int(n_vis), total)
     out = []
     for comp in range(3):
         # (time*baseline, channel) outer product, built in float64 then rounded once
-        col = np.multiply.outer(uvw_m[:, comp], np.asarray(freqs_hz) / C_LIGHT)
+        col = np.multiply.outer(uvw_m[:, comp], scale)
         out.append(col.reshape(-1)[:n_vis].astype(np.float32))
     return out[0], out[1], out[2]
 
@@ -166,6 +180,9 @@ class Workload:
     sky: PointSky | None = None
     noise_sigma: float = 0.0
     batch_offsets: np.ndarray | None = None
+    # the same coordinates by row and channel (u, v, w = rows_m[i // C] * chan_scale[i % C])
+    rows_m: np.ndarray | None = None
+    chan_scale: np.ndarray | None = None
 
     @property
     def n_vis(self) -> int:
@@ -182,9 +199,10 @@ def tiny(n_vis: int = 10_000, n: int = 256, fov: float = 0.1, n_w: int = 8, seed
 def array(n_dumps: int = 144, seed_extra: int = 0):
     rng = rng_for(2, seed_extra)
     freqs = np.linspace(120e6, 168e6, 16)
-    u, v, w = array_uvw(60, 20_000.0, n_dumps, freqs, rng)
+    rows, scale = array_rows(60, 20_000.0, n_dumps, freqs, rng)
+    u, v, w = expand_tracks(rows, scale)
     sky = power_law_sky(200, 0.1, 0.01, 1.0, rng)
-    return Workload("array", 4096, 0.2, 32, 7, 0.0, 0.0, u, v, w, sky=sky)
+    return Workload("array", 4096, 0.2, 32, 7, 0.0, 0.0, u, v, w, sky=sky, rows_m=rows, chan_scale=scale)
 
 
 def large(n_vis: int = 100_000_000, seed_extra: int = 0):
@@ -192,8 +210,9 @@ def large(n_vis: int = 100_000_000, seed_extra: int = 0):
     freqs = np.linspace(120e6, 168e6, 64)
     per_dump = 300 * 299 // 2 * 64
     n_dumps = -(-n_vis // per_dump)
-    u, v, w = array_uvw(300, 20_000.0, n_dumps, freqs, rng, n_vis=n_vis)
-    return Workload("large", 16384, 0.5, 32, 7, 0.0, 0.0, u, v, w)
+    rows, scale = array_rows(300, 20_000.0, n_dumps, freqs, rng)
+    u, v, w = expand_tracks(rows, scale, n_vis)
+    return Workload("large", 16384, 0.5, 32, 7, 0.0, 0.0, u, v, w, rows_m=rows, chan_scale=scale)
 
 
 def batched_counts(n_images: int = 64, lo: float = 1e5, hi: float = 2e6, seed_extra: int = 0):

@@ -522,3 +522,45 @@ def test_oversampled_image_within_half_band_aliasing_bound():
     assert np.all(err <= bound * (1 + 1e-9) + 1e-9)
     plain = np.abs(oracle.image(cfg, u, v, w, vis) - d)
     assert err.max() < 2e-3 * np.abs(d).max() and err.max() * 20 < plain.max()
+
+
+# ------------------------------------------------------------------------------------------
+# inputs by row and channel (the layout of the LOFAR datasets of section 4)
+# ------------------------------------------------------------------------------------------
+
+def test_expand_rows_exact_products_and_order():
+    """Products of dyadic numbers are exact, so every coordinate is known by hand; the
+    channel index runs fastest and the last row may be partial."""
+    rows = np.array([[3.0, -5.0, 0.25], [-7.0, 1.5, -2.0]])
+    scale = np.array([0.5, 2.0, 1.25])
+    u, v, w = oracle.expand_rows(rows, scale, 5)
+    np.testing.assert_array_equal(u, np.float32([1.5, 6.0, 3.75, -3.5, -14.0]))
+    np.testing.assert_array_equal(v, np.float32([-2.5, -10.0, -6.25, 0.75, 3.0]))
+    np.testing.assert_array_equal(w, np.float32([0.125, 0.5, 0.3125, -1.0, -4.0]))
+    assert all(a.dtype == np.float32 for a in (u, v, w))
+    with pytest.raises(ValueError):
+        oracle.expand_rows(rows, scale, 7)
+
+
+def test_expand_rows_rounds_the_fp64_product_once():
+    """(1 + 2^-24 + 2^-30)(1 - 2^-30) = 1 + 2^-24 - 2^-54 - 2^-60: FP64 rounds it to
+    1 + 2^-24, which FP32 rounds (tie to even) to 1.  Rounding the factors to FP32
+    first gives (1 + 2^-23) * 1 instead."""
+    x = 1.0 + 2.0 ** -24 + 2.0 ** -30
+    s = 1.0 - 2.0 ** -30
+    exact = Fraction(x) * Fraction(s)
+    assert exact == 1 + Fraction(1, 2 ** 24) - Fraction(1, 2 ** 54) - Fraction(1, 2 ** 60)
+    u, v, w = oracle.expand_rows([[x, -x, x]], [s], 1)
+    assert u[0] == np.float32(1.0) and v[0] == np.float32(-1.0) and w[0] == np.float32(1.0)
+    assert np.float32(x) * np.float32(s) == np.float32(1.0 + 2.0 ** -23)
+
+
+def test_expand_rows_matches_the_workload_tracks():
+    """The track generator's per-visibility coordinates and its rows x channels agree
+    (the bench passes the same workload either way)."""
+    work = synth.array(n_dumps=6)
+    u, v, w = oracle.expand_rows(work.rows_m, work.chan_scale, work.n_vis)
+    np.testing.assert_array_equal(u, work.u)
+    np.testing.assert_array_equal(v, work.v)
+    np.testing.assert_array_equal(w, work.w)
+    assert work.n_vis == work.rows_m.shape[0] * work.chan_scale.size
