@@ -387,6 +387,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         k = np.clip(np.floor((work.w.astype(np.float64) - lo) * (work.n_w / (hi - lo))), 0, work.n_w - 1)
         work.w = (lo + (k + 0.5) * (hi - lo) / work.n_w).astype(np.float32)
         work.w_min, work.w_max = lo, hi
+        work.rows_m = work.chan_scale = None  # snapped w no longer follow the rows
     n_vis = work.n_vis
     batch = 1 if work.batch_offsets is None else len(work.batch_offsets) - 1
     dev = torch.device("cuda", local_rank)
@@ -481,11 +482,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     e2e = None
     if not args.no_e2e:
         h_img = torch.empty((batch, work.n, work.n), dtype=torch.complex64).pin_memory()
+        rows = work.rows_m is not None
+        if rows:
+            h_rows, h_scale = pin(work.rows_m), pin(work.chan_scale)
 
         def e2e_step():
             # the C ABI with host buffers: the sort reads the pinned inputs and the last
             # column pass writes the pinned image in place (host <-> device over NVLink-C2C)
             plan.set_vis(h_u, h_v, h_w, h_vis, None, offsets)
+            plan.image(out=h_img)
+
+        def rows_step():
+            # the same with the inputs as recorded: baseline coordinates per row (metres)
+            # and nu / c per channel, expanded to (u, v, w) inside the sort
+            plan.set_vis_rows(h_rows, h_scale, h_vis, None, offsets)
             plan.image(out=h_img)
 
         def copy_step():
@@ -515,13 +525,29 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
         e2e_ms = timed(e2e_step)
         copy_ms = timed(copy_step)
-        e2e = {"value": round(world * n_vis / (e2e_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
-               "h2d_bytes_per_step": int(20 * n_vis), "d2h_bytes_per_step": int(8 * batch * work.n * work.n),
-               "ms_per_step": round(e2e_ms, 3),
-               "transfer": "host buffers passed to wst_plan_set_vis / wst_image, read and written in place by "
-                           "the kernels (pinned memory, NVLink-C2C)",
-               "explicit_copies": {"value": round(world * n_vis / (copy_ms * 1e-3) / 1e6, 2),
-                                   "ms_per_step": round(copy_ms, 3)}}
+        d2h = int(8 * batch * work.n * work.n)
+        plain = {"value": round(world * n_vis / (e2e_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+                 "h2d_bytes_per_step": int(20 * n_vis), "d2h_bytes_per_step": d2h,
+                 "ms_per_step": round(e2e_ms, 3),
+                 "transfer": "host buffers passed to wst_plan_set_vis / wst_image, read and written in place by "
+                             "the kernels (pinned memory, NVLink-C2C)"}
+        copies = {"value": round(world * n_vis / (copy_ms * 1e-3) / 1e6, 2), "ms_per_step": round(copy_ms, 3),
+                  "transfer": "wst_plan_set_vis / wst_image on device buffers, cudaMemcpyAsync H2D / D2H around them"}
+        if rows:
+            rows_ms = timed(rows_step)
+            torch.cuda.synchronize(dev)
+            # the image of the last end-to-end step against the device-resident step's
+            diff = float((h_img.to(dev) - img).abs().max() / img.abs().max())
+            e2e = {"value": round(world * n_vis / (rows_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+                   "h2d_bytes_per_step": int(work.rows_m.nbytes + work.chan_scale.nbytes + 8 * n_vis),
+                   "d2h_bytes_per_step": d2h, "ms_per_step": round(rows_ms, 3),
+                   "transfer": "host buffers passed to wst_plan_set_vis_rows (baseline metres per row, nu / c "
+                               "per channel, values) and wst_image, read and written in place by the kernels "
+                               "(pinned memory, NVLink-C2C)",
+                   "image_max_diff_rel_peak_vs_device_step": diff,
+                   "per_visibility_coordinates": plain, "explicit_copies": copies}
+        else:
+            e2e = dict(plain, explicit_copies=copies)
         plan.stats()
 
     # accuracy: the image against the direct transform, with the stated per-pixel bound

@@ -178,6 +178,27 @@ wst_status wst_plan_set_vis(wst_plan plan, int64_t n_vis, const float *u, const 
                             const int64_t *batch_offsets);
 
 /*
+ * wst_plan_set_vis for visibilities laid out by row and channel, as an interferometer
+ * records them (one row = one baseline at one time; the LOFAR datasets of section 4
+ * are of this shape, sub-bands split into channels): visibility i belongs to row
+ * r = i / n_chan and channel c = i % n_chan,
+ * and its coordinates in wavelengths are
+ *     (u, v, w)_i = fl32(uvw_m[3 r + k] * chan_scale[c]),  k = 0, 1, 2,
+ * the product of the row's baseline coordinates in metres and the channel's nu / c,
+ * formed in FP64 and rounded once to FP32.  The result is exactly that of
+ * wst_plan_set_vis with those u, v, w; the inputs shrink from 20 to 8 bytes per
+ * visibility plus 24 per row (plus 4 per visibility with weights).
+ * uvw_m: FP64 [n_rows x 3]; chan_scale: FP64 [n_chan]; vis, weight, batch_offsets as
+ * for wst_plan_set_vis (index i).  n_vis <= n_rows * n_chan (the last row may be
+ * partial).  Every array may be device memory or page-locked host memory (read in
+ * place).  Errors: INVALID_ARG (n_chan < 1, n_rows too small, NULL or unreachable
+ * arrays), OOM, CUDA.
+ */
+wst_status wst_plan_set_vis_rows(wst_plan plan, int64_t n_vis, const double *uvw_m, int64_t n_rows,
+                                 const double *chan_scale, int32_t n_chan, const void *vis,
+                                 const float *weight, const int64_t *batch_offsets);
+
+/*
  * Eq. 3: grid planes [plane_begin, plane_end) (global plane index image*N_w + k)
  * into grid_out, complex64 [(plane_end - plane_begin) x M x M], natural layout, M the
  * grid side (N, or 2N with oversample = 2).

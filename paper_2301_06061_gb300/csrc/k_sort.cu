@@ -23,13 +23,14 @@ __device__ __forceinline__ bool finite2(float2 a) { return isfinite(a.x) && isfi
 
 // per image min / max of the finite w (order-preserving integer encoding)
 // (fold: of |w|, the w of the mirrored visibilities)
-__global__ void k_wrange(const float *w, const int64_t *boff, uint32_t *wminmax, bool fold) {
+template <bool ROWS>
+__global__ void k_wrange(VisCoords coords, const int64_t *boff, uint32_t *wminmax, bool fold) {
   const int img = blockIdx.y;
   const int64_t b0 = boff[img], b1 = boff[img + 1];
   uint32_t mn = 0xFFFFFFFFu, mx = 0u;
   for (int64_t j = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b1;
        j += (int64_t)gridDim.x * blockDim.x) {
-    float x = w[j];
+    float x = coords_w<ROWS>(coords, j);
     if (fold) x = fabsf(x);
     if (isfinite(x)) {
       uint32_t o = float_to_ordered(x);
@@ -122,9 +123,11 @@ __device__ __forceinline__ void frac_ff(float hi, float lo, float &fl, float &e0
   e1 = __fsub_rn(__fsub_rn(1.0f, fr), lo);
 }
 
-// pass 1: placement, bucket key, histogram rank (warp-aggregated atomics)
-__global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, const float *__restrict__ v,
-                       const float *__restrict__ w, const float2 *__restrict__ vis,
+// pass 1: placement, bucket key, histogram rank (warp-aggregated atomics); ROWS: the
+// coordinates come from rows and channels (one instance each, so that the plain one
+// keeps its registers)
+template <bool ROWS>
+__global__ void __launch_bounds__(256, 5) k_keys(VisCoords coords, const float2 *__restrict__ vis,
                        const float *__restrict__ weight, const int64_t *__restrict__ boff,
                        const double *__restrict__ wrange, const float4 *__restrict__ wrange_ff, SortGeom g,
                        uint32_t *offsets, uint4 *keyinfo, unsigned long long *counters,
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(256, 5) k_keys(const float *__restrict__ u, co
     bool nonfinite = false, dropped = false, kept = false;
     uint32_t key = kDropKey, xpack = 0, ypack = 0, mirrored = 0;
     if (in) {
-      float uf = u[j], vf = v[j], wf = w[j];
+      float uf, vf, wf;
+      coords_uvw<ROWS>(coords, j, uf, vf, wf);
       if (fold && wf < 0.0f) {  // Hermitian mirror (exact sign flips); the scatter conjugates V
         uf = -uf;
         vf = -vf;
@@ -446,8 +450,8 @@ static unsigned grid_for(int64_t n, int threads, int max_blocks) {
   return (unsigned)b;
 }
 
-cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
-                              const float2 *vis, const float *weight, bool host_inputs) {
+cudaError_t sort_visibilities(wst_plan_s *p, const VisCoords &coords, const float2 *vis, const float *weight,
+                              bool host_inputs) {
   // inputs in host memory are read once: the placement pass leaves value and weight in
   // device memory for the scatter
   float4 *stash = host_inputs ? p->W_.stash : nullptr;
@@ -466,7 +470,8 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   dim3 grd(grid_for(avg, 256, 4096), p->batch);
   const bool fold = (p->cfg.flags & WST_FLAG_WFOLD) != 0;
   if (p->cfg.w_min == p->cfg.w_max) {
-    k_wrange<<<grd, 256, 0, s>>>(w, p->batch_off, ws.wminmax, fold);
+    if (coords.rows) k_wrange<true><<<grd, 256, 0, s>>>(coords, p->batch_off, ws.wminmax, fold);
+    else k_wrange<false><<<grd, 256, 0, s>>>(coords, p->batch_off, ws.wminmax, fold);
     p->launches += 1;
   }
   if ((e = build_plane_centres(p))) return e;
@@ -481,8 +486,12 @@ cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, con
   g.fov_lo = (float)(g.fov - (double)g.fov_hi);
   g.half_nf = (float)g.half_n;
   g.half_wf = (float)g.half_w;
-  k_keys<<<grd, 256, 0, s>>>(u, v, w, vis, weight, p->batch_off, p->wrange, p->wrange_ff, g, ws.offsets,
-                               ws.keyinfo, ws.counters, stash, fold);
+  if (coords.rows)
+    k_keys<true><<<grd, 256, 0, s>>>(coords, vis, weight, p->batch_off, p->wrange, p->wrange_ff, g, ws.offsets,
+                                     ws.keyinfo, ws.counters, stash, fold);
+  else
+    k_keys<false><<<grd, 256, 0, s>>>(coords, vis, weight, p->batch_off, p->wrange, p->wrange_ff, g, ws.offsets,
+                                      ws.keyinfo, ws.counters, stash, fold);
   p->launches += 1;
   if ((e = cudaGetLastError())) return e;
   if ((e = scan_exclusive(ws.offsets, nb1, ws.scan_tmp, s, p->launches))) return e;

@@ -294,21 +294,15 @@ static const void *device_view(const wst_plan_s *p, const void *ptr, bool *is_ho
   return pageable ? ptr : nullptr;
 }
 
-wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const float *v, const float *w,
-                            const void *vis, const float *weight, const int64_t *batch_offsets) {
-  if (!p) return WST_ERR_INVALID_ARG;
-  p->vis_set = false;
-  if (n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return fail(p, WST_ERR_INVALID_ARG, "n_vis out of range");
-  if (n_vis > 0 && (!u || !v || !w || !vis)) return fail(p, WST_ERR_INVALID_ARG, "NULL visibility array");
+// The part of wst_plan_set_vis and wst_plan_set_vis_rows after their coordinate
+// arguments are checked: values, weights, batch offsets, workspace, then the sort.
+static wst_status set_vis_common(wst_plan_s *p, int64_t n_vis, const VisCoords &coords, const void *vis,
+                                 const float *weight, const int64_t *batch_offsets) {
   bool host_vis = false;
   if (n_vis > 0) {
-    const void *du = device_view(p, u), *dv = device_view(p, v), *dw = device_view(p, w);
     const void *dvis = device_view(p, vis, &host_vis), *dwt = weight ? device_view(p, weight) : nullptr;
-    if (!du || !dv || !dw || !dvis || (weight && !dwt))
+    if (!dvis || (weight && !dwt))
       return fail(p, WST_ERR_INVALID_ARG, "visibility arrays must be device or page-locked host memory");
-    u = (const float *)du;
-    v = (const float *)dv;
-    w = (const float *)dw;
     vis = dvis;
     weight = (const float *)dwt;
   }
@@ -354,11 +348,49 @@ wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const flo
   p->n_vis = n_vis;
   p->has_weight = weight != nullptr;
   WST_CUDA(p, time_begin(p, p->ev_sort, ST_SORT), "event");
-  WST_CUDA(p, sort_visibilities(p, u, v, w, (const float2 *)vis, weight, host_vis), "sort");
+  WST_CUDA(p, sort_visibilities(p, coords, (const float2 *)vis, weight, host_vis), "sort");
   WST_CUDA(p, time_end(p, p->ev_sort), "event");
   p->launches_sort = p->launches;
   p->vis_set = true;
   return WST_OK;
+}
+
+wst_status wst_plan_set_vis(wst_plan p, int64_t n_vis, const float *u, const float *v, const float *w,
+                            const void *vis, const float *weight, const int64_t *batch_offsets) {
+  if (!p) return WST_ERR_INVALID_ARG;
+  p->vis_set = false;
+  if (n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return fail(p, WST_ERR_INVALID_ARG, "n_vis out of range");
+  if (n_vis > 0 && (!u || !v || !w || !vis)) return fail(p, WST_ERR_INVALID_ARG, "NULL visibility array");
+  VisCoords c;
+  if (n_vis > 0) {
+    c.u = (const float *)device_view(p, u);
+    c.v = (const float *)device_view(p, v);
+    c.w = (const float *)device_view(p, w);
+    if (!c.u || !c.v || !c.w)
+      return fail(p, WST_ERR_INVALID_ARG, "visibility arrays must be device or page-locked host memory");
+  }
+  return set_vis_common(p, n_vis, c, vis, weight, batch_offsets);
+}
+
+wst_status wst_plan_set_vis_rows(wst_plan p, int64_t n_vis, const double *uvw_m, int64_t n_rows,
+                                 const double *chan_scale, int32_t n_chan, const void *vis, const float *weight,
+                                 const int64_t *batch_offsets) {
+  if (!p) return WST_ERR_INVALID_ARG;
+  p->vis_set = false;
+  if (n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return fail(p, WST_ERR_INVALID_ARG, "n_vis out of range");
+  if (n_chan < 1 || n_rows < 0) return fail(p, WST_ERR_INVALID_ARG, "n_chan must be >= 1 and n_rows >= 0");
+  if (n_vis > 0 && (n_vis - 1) / n_chan >= n_rows)
+    return fail(p, WST_ERR_INVALID_ARG, "n_vis exceeds n_rows * n_chan");
+  if (n_vis > 0 && (!uvw_m || !chan_scale || !vis)) return fail(p, WST_ERR_INVALID_ARG, "NULL visibility array");
+  VisCoords c;
+  c.n_chan = (uint32_t)n_chan;
+  if (n_vis > 0) {
+    c.rows = (const double *)device_view(p, uvw_m);
+    c.scale = (const double *)device_view(p, chan_scale);
+    if (!c.rows || !c.scale)
+      return fail(p, WST_ERR_INVALID_ARG, "row and channel arrays must be device or page-locked host memory");
+  }
+  return set_vis_common(p, n_vis, c, vis, weight, batch_offsets);
 }
 
 static wst_status check_ready(wst_plan_s *p) {

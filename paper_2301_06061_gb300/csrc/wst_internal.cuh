@@ -255,9 +255,42 @@ cudaError_t build_tables(wst_plan_s *p);
 cudaError_t build_correction(wst_plan_s *p);
 cudaError_t build_plane_centres(wst_plan_s *p);
 
+// Where the sort reads the (u, v, w) of visibility j: per-visibility FP32 arrays, or
+// (rows != nullptr) a row of FP64 metres times a channel's nu / c, the product in FP64
+// rounded once to FP32, for visibility j = row * n_chan + channel.
+struct VisCoords {
+  const float *u = nullptr, *v = nullptr, *w = nullptr;
+  const double *rows = nullptr;   // [n_rows][3] u, v, w in metres
+  const double *scale = nullptr;  // [n_chan] nu / c
+  uint32_t n_chan = 1;
+};
+template <bool ROWS>
+__device__ __forceinline__ void coords_uvw(const VisCoords &c, int64_t j, float &u, float &v, float &w) {
+  if constexpr (ROWS) {
+    const uint32_t r = (uint32_t)j / c.n_chan, ch = (uint32_t)j - r * c.n_chan;  // j < 2^32
+    const double s = c.scale[ch];
+    const double *m = c.rows + 3 * (size_t)r;
+    u = __double2float_rn(__dmul_rn(m[0], s));
+    v = __double2float_rn(__dmul_rn(m[1], s));
+    w = __double2float_rn(__dmul_rn(m[2], s));
+  } else {
+    u = c.u[j];
+    v = c.v[j];
+    w = c.w[j];
+  }
+}
+template <bool ROWS>
+__device__ __forceinline__ float coords_w(const VisCoords &c, int64_t j) {
+  if constexpr (ROWS) {
+    const uint32_t r = (uint32_t)j / c.n_chan, ch = (uint32_t)j - r * c.n_chan;
+    return __double2float_rn(__dmul_rn(c.rows[3 * (size_t)r + 2], c.scale[ch]));
+  }
+  return c.w[j];
+}
+
 // k_sort.cu
-cudaError_t sort_visibilities(wst_plan_s *p, const float *u, const float *v, const float *w,
-                              const float2 *vis, const float *weight, bool host_inputs);
+cudaError_t sort_visibilities(wst_plan_s *p, const VisCoords &coords, const float2 *vis, const float *weight,
+                              bool host_inputs);
 cudaError_t vis_cells(wst_plan_s *p, int32_t *plane, int32_t *i0, int32_t *j0, int64_t n_bound);
 int64_t scan_tmp_words(int64_t n);
 

@@ -29,7 +29,7 @@ WST_NO_CORRECTION = 0x1
 EXPORTED = [
     "wst_version", "wst_status_string", "wst_plan_create", "wst_plan_destroy", "wst_plan_set_stream",
     "wst_plan_workspace_bytes", "wst_plan_set_workspace", "wst_plan_set_kernel_table",
-    "wst_plan_set_vis", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_degrid",
+    "wst_plan_set_vis", "wst_plan_set_vis_rows", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_degrid",
     "wst_kernel_grad", "wst_vis_cells", "wst_get_stats", "wst_last_error", "wst_dft",
     "wst_predict_points", "wst_dft_noalloc",
 ]
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "wst_plan_set_workspace": ([P, P, ctypes.c_size_t], ctypes.c_int),
             "wst_plan_set_kernel_table": ([P, P], ctypes.c_int),
             "wst_plan_set_vis": ([P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "wst_plan_set_vis_rows": ([P, I64, P, I64, P, I32, P, P, P], ctypes.c_int),
             "wst_grid": ([P, I32, I32, P], ctypes.c_int),
             "wst_fft_correct": ([P, I32, I32, P, P], ctypes.c_int),
             "wst_correct": ([P, P], ctypes.c_int),
@@ -208,6 +209,25 @@ def wst_plan_set_vis(plan, u, v, w, vis, weight=None, batch_offsets=None) -> Non
     _check(load_library().wst_plan_set_vis(plan, n, _ptr(u, h), _ptr(v, h), _ptr(w, h), _ptr(vis, h),
                                            _ptr(weight, h), off),
            "wst_plan_set_vis", plan)
+
+
+def wst_plan_set_vis_rows(plan, uvw_m, chan_scale, vis, weight=None, batch_offsets=None) -> None:
+    """Visibility i = row (i // n_chan), channel (i % n_chan); uvw_m FP64 [n_rows, 3] metres,
+    chan_scale FP64 [n_chan] (nu / c), vis complex64 [n_vis] with n_vis <= n_rows * n_chan."""
+    n = vis.numel()
+    assert uvw_m.dtype == torch.float64 and uvw_m.dim() == 2 and uvw_m.shape[1] == 3
+    assert chan_scale.dtype == torch.float64 and chan_scale.dim() == 1
+    assert vis.dtype == torch.complex64
+    if weight is not None:
+        assert weight.dtype == torch.float32 and weight.numel() == n
+    off = None
+    if batch_offsets is not None:
+        arr = (ctypes.c_int64 * len(batch_offsets))(*[int(x) for x in batch_offsets])
+        off = ctypes.cast(arr, ctypes.c_void_p)
+    h = True  # device tensors or pinned host tensors
+    _check(load_library().wst_plan_set_vis_rows(plan, n, _ptr(uvw_m, h), uvw_m.shape[0], _ptr(chan_scale, h),
+                                                chan_scale.numel(), _ptr(vis, h), _ptr(weight, h), off),
+           "wst_plan_set_vis_rows", plan)
 
 
 def wst_grid(plan, plane_begin: int, plane_end: int, grid_out: torch.Tensor) -> None:
@@ -344,6 +364,12 @@ class Plan:
         wst_plan_stream(self.handle)
         wst_plan_set_vis(self.handle, u, v, w, vis, weight, batch_offsets)
         self.n_vis = u.numel()
+
+    def set_vis_rows(self, uvw_m, chan_scale, vis, weight=None, batch_offsets=None):
+        self.ensure_workspace(vis.numel())
+        wst_plan_stream(self.handle)
+        wst_plan_set_vis_rows(self.handle, uvw_m, chan_scale, vis, weight, batch_offsets)
+        self.n_vis = vis.numel()
 
     def image(self, out=None, flags: int = 0) -> torch.Tensor:
         c = self.cfg

@@ -309,6 +309,90 @@ def test_pageable_or_foreign_host_tensors_rejected_by_binding(wst):
         wst._ptr(torch.zeros(4).pin_memory())  # host memory where only device memory is accepted
 
 
+def rows_case(n, seed, n_dumps=3, n_stations=24, n_chan=8, partial=5):
+    """Earth-rotation tracks by row and channel, baselines reaching about 0.8 of the grid's
+    half-width at the top channel, the last row partial; random values and weights."""
+    rng = np.random.default_rng(seed)
+    freqs = np.linspace(120e6, 168e6, n_chan)
+    rows, scale = synth.array_rows(n_stations, 0.7 * n / 0.1, n_dumps, freqs, rng)
+    n_vis = rows.shape[0] * n_chan - partial
+    vis = synth.random_visibilities(n_vis, rng)
+    weight = rng.uniform(0.5, 2.0, n_vis).astype(np.float32)
+    return rows, scale, vis, weight
+
+
+def cells(wst, plan, n_vis):
+    k = torch.empty(n_vis, dtype=torch.int32, device="cuda")
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    return k.cpu().numpy(), i0.cpu().numpy(), j0.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [256, 8192])
+def test_set_vis_rows_placement_and_image(wst, n):
+    """wst_plan_set_vis_rows: the coordinates formed in the sort (FP64 product of the
+    row's metres and the channel's nu / c, one rounding) place every visibility where the
+    oracle's expansion does, the w range from the data included, and the image (weights,
+    a partial last row) matches the oracle."""
+    rows, scale, vis, weight = rows_case(n, seed=51 + n)
+    u, v, w = oracle.expand_rows(rows, scale, vis.size)
+    cfg = wst.Config(n=n, fov=0.1, n_w=4, flags=wst.WST_FLAG_KAHAN)  # w range from the data
+    plan = wst.Plan(cfg)
+    plan.set_vis_rows(dev(rows), dev(scale), dev(vis), dev(weight))
+    lo, hi = oracle.resolve_w_range(w, 0.0, 0.0)
+    st_ = plan.stats()
+    assert st_["w_min"] == lo and st_["w_max"] == hi
+    oc = ocfg_for(cfg, lo, hi)
+    ko, io, jo, status = oracle.locate(oc, u, v, w, vis, weight)
+    k, i0, j0 = cells(wst, plan, vis.size)
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(i0, io)
+    np.testing.assert_array_equal(j0, jo)
+    assert st_["n_kept"] == int((status == 0).sum()) > 0.9 * vis.size
+    img = plan.image()
+    assert_image_parity(img[0].cpu().numpy(), oracle.image(oc, u, v, w, vis, weight), oc)
+
+
+def test_set_vis_rows_pinned_host_and_batched(wst):
+    """Rows, scales, values and weights in page-locked host memory, two images split by
+    batch offsets: the images equal those of wst_plan_set_vis on device copies of the
+    expanded coordinates (uncorrected; up to the order of float atomics)."""
+    rows, scale, vis, weight = rows_case(256, seed=61, n_dumps=4)
+    u, v, w = oracle.expand_rows(rows, scale, vis.size)
+    off = [0, vis.size // 3, vis.size]
+    cfg = wst.Config(n=256, fov=0.1, n_w=3, batch=2)  # per-image w ranges from the data
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    plan = wst.Plan(cfg)
+    plan.set_vis_rows(pin(rows), pin(scale), pin(vis), pin(weight), off)
+    host_img = torch.empty((2, 256, 256), dtype=torch.complex64).pin_memory()
+    plan.image(out=host_img, flags=wst.WST_NO_CORRECTION)
+    torch.cuda.synchronize()
+    k, i0, j0 = cells(wst, plan, vis.size)
+    ref_plan = gpu_plan(wst, cfg, u, v, w, vis, weight, off)
+    kr, ir, jr = cells(wst, ref_plan, vis.size)
+    np.testing.assert_array_equal(k, kr)
+    np.testing.assert_array_equal(i0, ir)
+    np.testing.assert_array_equal(j0, jr)
+    ref = ref_plan.image(flags=wst.WST_NO_CORRECTION).cpu().numpy()
+    for b in range(2):
+        assert rel_err(host_img[b].numpy(), ref[b]) < 1e-6
+
+
+def test_set_vis_rows_rejects_bad_arguments(wst):
+    cfg = wst.Config(n=256, fov=0.1, n_w=2, w_min=-200.0, w_max=200.0)
+    plan = wst.Plan(cfg)
+    rows = dev(np.zeros((2, 3)))
+    vis = dev(np.zeros(7, np.complex64))
+    with pytest.raises(wst.WstError):  # 7 visibilities > 2 rows x 3 channels
+        plan.set_vis_rows(rows, dev(np.ones(3)), vis)
+    with pytest.raises(wst.WstError):  # no channels
+        plan.set_vis_rows(rows, dev(np.ones(0)), dev(np.zeros(1, np.complex64)))
+    with pytest.raises(ValueError):  # pageable host rows
+        plan.set_vis_rows(torch.zeros((2, 3), dtype=torch.float64), dev(np.ones(3)), vis[:6])
+    plan.set_vis_rows(rows, dev(np.ones(3)), vis[:6])  # exactly full rows
+    assert plan.stats()["n_kept"] == 6
+
+
 @pytest.mark.parametrize("n", [256, 8192])
 def test_wfold_placement_and_image(wst, n):
     """WST_FLAG_WFOLD: w < 0 visibilities are mirrored before placement (the w range from
