@@ -84,6 +84,22 @@ def load_peaks():
 # workloads (seeded, synthetic; see paper_2301_06061_gb300/synth.py)
 # ------------------------------------------------------------------------------------------
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mvis(world: int, n_vis: int, ms: float) -> float:
+    """Whole-job throughput in Mvis/s: every rank images its own n_vis visibilities in ms."""
+    return world * n_vis / (ms * 1e-3) / 1e6
+
+
 def make_workload(name: str, rank: int, n_w: int = 0, vis_frac: float = 1.0):
     from paper_2301_06061_gb300 import synth
 
@@ -445,12 +461,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
     st = plan.stats()
-    ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * n_vis / (ms_step * 1e-3) / 1e6
+    ms_step = max_over_ranks(ms_total / args.steps, dist, dev)
+    value = job_mvis(world, n_vis, ms_step)
 
     # stage times inside the timed region (CUDA events on the plan's stream)
     stages = {"sort": st["ms_sort"], "grid": st["ms_grid"], "rows": st["ms_rows"], "cols_a": st["ms_cols_a"],
@@ -516,29 +528,24 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 fn()
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1) / n_e2e
-            if dist:
-                t = torch.tensor([ms], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms = float(t.item())
-            return ms
+            return max_over_ranks(e0.elapsed_time(e1) / n_e2e, dist, dev)
 
         e2e_ms = timed(e2e_step)
         copy_ms = timed(copy_step)
         d2h = int(8 * batch * work.n * work.n)
-        plain = {"value": round(world * n_vis / (e2e_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+        plain = {"value": round(job_mvis(world, n_vis, e2e_ms), 2), "unit": "Mvis/s",
                  "h2d_bytes_per_step": int(20 * n_vis), "d2h_bytes_per_step": d2h,
                  "ms_per_step": round(e2e_ms, 3),
                  "transfer": "host buffers passed to wst_plan_set_vis / wst_image, read and written in place by "
                              "the kernels (pinned memory, NVLink-C2C)"}
-        copies = {"value": round(world * n_vis / (copy_ms * 1e-3) / 1e6, 2), "ms_per_step": round(copy_ms, 3),
+        copies = {"value": round(job_mvis(world, n_vis, copy_ms), 2), "ms_per_step": round(copy_ms, 3),
                   "transfer": "wst_plan_set_vis / wst_image on device buffers, cudaMemcpyAsync H2D / D2H around them"}
         if rows:
             rows_ms = timed(rows_step)
             torch.cuda.synchronize(dev)
             # the image of the last end-to-end step against the device-resident step's
             diff = float((h_img.to(dev) - img).abs().max() / img.abs().max())
-            e2e = {"value": round(world * n_vis / (rows_ms * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+            e2e = {"value": round(job_mvis(world, n_vis, rows_ms), 2), "unit": "Mvis/s",
                    "h2d_bytes_per_step": int(work.rows_m.nbytes + work.chan_scale.nbytes + 8 * n_vis),
                    "d2h_bytes_per_step": d2h, "ms_per_step": round(rows_ms, 3),
                    "transfer": "host buffers passed to wst_plan_set_vis_rows (baseline metres per row, nu / c "
@@ -580,7 +587,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "ggpas": {"end_to_end": round(n_vis * cfg.support ** 2 / (ms_step * 1e-3) / 1e9, 2),
+            "ggpas": {"step": round(n_vis * cfg.support ** 2 / (ms_step * 1e-3) / 1e9, 2),
                       "grid_kernel": round(n_vis * cfg.support ** 2 / (stages["grid"] / args.steps * 1e-3) / 1e9, 2),
                       "note": "grid-point additions per second (N_vis W^2 / time); the grid kernel also "
                               "transforms the rows"},
