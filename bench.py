@@ -301,6 +301,21 @@ def stage_bytes(stage: str, n: int, planes: int, chunks: int, batch: int, n_kept
     raise ValueError(stage)
 
 
+def step_roofline(stage_ms: dict, n: int, planes: int, chunks: int, batch: int, n_kept: int, n_vis: int,
+                  oversample: int, ms_step: float, peak: float) -> dict:
+    """The whole step against HBM: the algorithmic bytes of every stage that ran (per
+    step), and the all-resident floor of 4 S per plane (grid write, two column passes
+    that read and write, counted as S + 2S + S) plus one image write."""
+    launches = {"sort": 1, "grid": chunks, "rows": chunks, "cols_a": chunks, "cols_b": chunks}
+    total = sum(stage_bytes(k, n, planes, chunks, batch, n_kept, n_vis, oversample) * launches[k]
+                for k, ms in stage_ms.items() if ms > 0)
+    floor = 4.0 * planes * 8.0 * (n * oversample) ** 2 + batch * 8.0 * n * n
+    sec = ms_step * 1e-3
+    return {"bytes": total, "ms": round(ms_step, 3), "achieved": round(total / sec / 1e9, 1),
+            "frac": round(total / sec / 1e9 / peak, 4), "all_resident_floor_bytes": floor,
+            "frac_of_all_resident_floor": round(floor / sec / 1e9 / peak, 4)}
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_2301_06061_gb300", "csrc"))):
@@ -489,6 +504,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                                            n_vis, osf) * launches_per_stage[k] /
                                                (v / args.steps * 1e-3) / 1e9 / peak, 4)
                                       for k, v in stages.items() if v > 0}}
+    roofline["step"] = step_roofline({k: v / args.steps for k, v in stages.items()}, work.n, planes,
+                                     st["n_chunks"], batch, st["n_kept"], n_vis, osf, ms_step, peak)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
