@@ -19,10 +19,14 @@ The paper grids with a Gaussian of 7 cells (section 2, Eq. 3) and lists better
   in the central 3/4 of the image; prediction = U(table) (``autograd.kernel_image``:
   ``wst_image`` forward, ``wst_kernel_grad`` backward) times the correction; loss =
   relative squared error; Adam on the MLP parameters.
+* ``save_checkpoint`` / ``load_checkpoint``: the training state (MLP parameters, Adam's
+  moments, completed steps, losses) written atomically every few steps, so that an
+  interrupted training resumes where it stopped and ends as an uninterrupted one does.
 """
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -162,11 +166,17 @@ class Trainer:
             errs = [math.sqrt(float(self.loss(table.detach(), self.sky_case(i)))) for i in indices]
         return float(np.mean(errs))
 
-    def train(self, mlp: KernelMLP, indices, lr: float = 1e-3, log_every: int = 0):
+    def train(self, mlp: KernelMLP, indices, lr: float = 1e-3, log_every: int = 0, checkpoint: str | None = None,
+              checkpoint_every: int = 0):
+        """One Adam step per sky of ``indices``; with ``checkpoint``, resume from it if it
+        exists and rewrite it every ``checkpoint_every`` steps."""
         opt = torch.optim.Adam(mlp.parameters(), lr=lr)
-        history = []
-        for step, i in enumerate(indices):
-            case = self.sky_case(i)
+        indices = list(indices)
+        start, history = 0, []
+        if checkpoint and os.path.exists(checkpoint):
+            start, history = load_checkpoint(checkpoint, mlp, opt)
+        for step in range(start, len(indices)):
+            case = self.sky_case(indices[step])
             opt.zero_grad()
             table = tabulate(mlp, self.support, self.per_cell, self.device)
             loss = self.loss(table, case)
@@ -175,17 +185,37 @@ class Trainer:
             history.append(float(loss.item()))
             if log_every and step % log_every == 0:
                 print(f"step {step} loss {history[-1]:.4e}", flush=True)
+            if checkpoint and checkpoint_every and (step + 1) % checkpoint_every == 0:
+                save_checkpoint(checkpoint, mlp, opt, step + 1, history)
         return history
 
 
-def train_default(n_skies: int = 10_000, held_out: int = 500, device="cuda", log_every: int = 500):
+def save_checkpoint(path: str, mlp: KernelMLP, opt: torch.optim.Optimizer, step: int, history) -> None:
+    """Training state after ``step`` completed steps; written to a temporary file and
+    renamed, so a crash while saving leaves the previous checkpoint intact."""
+    tmp = path + ".tmp"
+    torch.save({"mlp": mlp.state_dict(), "opt": opt.state_dict(), "step": int(step),
+                "history": [float(h) for h in history]}, tmp)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, mlp: KernelMLP, opt: torch.optim.Optimizer):
+    """Restore parameters and optimiser state in place; returns (completed steps, losses)."""
+    state = torch.load(path, map_location="cpu")
+    mlp.load_state_dict(state["mlp"])
+    opt.load_state_dict(state["opt"])
+    return int(state["step"]), list(state["history"])
+
+
+def train_default(n_skies: int = 10_000, held_out: int = 500, device="cuda", log_every: int = 500,
+                  checkpoint: str | None = None, checkpoint_every: int = 500):
     """The full training of the learned W = 8 kernel; returns (mlp, table, report)."""
     torch.manual_seed(20230106)
     mlp = KernelMLP(8).to(device)
     gauss = gaussian_table(8, wst.DEFAULT_SIGMA[8], device=device)
     fit_to_table(mlp, gauss, 8, 1024)
     tr = Trainer(device=device)
-    tr.train(mlp, range(n_skies), log_every=log_every)
+    tr.train(mlp, range(n_skies), log_every=log_every, checkpoint=checkpoint, checkpoint_every=checkpoint_every)
     table = tabulate(mlp, 8, 1024, device).detach()
     test_idx = range(1_000_000, 1_000_000 + held_out)
     report = {"gauss_err": tr.evaluate(gauss, test_idx), "learned_err": tr.evaluate(table, test_idx)}
@@ -218,9 +248,12 @@ if __name__ == "__main__":
     ap.add_argument("--skies", type=int, default=10_000)
     ap.add_argument("--held-out", type=int, default=500)
     ap.add_argument("--out", default="learned_kernel_w8.npz")
+    ap.add_argument("--checkpoint", default=None, help="resume from / save the training state to this file")
+    ap.add_argument("--checkpoint-every", type=int, default=500)
     a = ap.parse_args()
     t0 = time.time()
-    mlp, table, report = train_default(a.skies, a.held_out)
+    mlp, table, report = train_default(a.skies, a.held_out, checkpoint=a.checkpoint,
+                                       checkpoint_every=a.checkpoint_every)
     report.update({"skies": a.skies, "held_out": a.held_out, "train_seconds": time.time() - t0})
     save(a.out, mlp, table, report)
     print(json.dumps(report))

@@ -30,3 +30,45 @@ def test_mlp_kernel_is_even_and_tabulated_on_the_support():
     tab = learned.tabulate(mlp, 8, per_cell=4)
     assert tab.shape == (33,)
     assert torch.allclose(tab, torch.flip(tab, [0]))
+
+
+def _cpu_trainer(learned):
+    """A Trainer whose sky and loss are host stand-ins (no plan, no GPU): the training
+    loop, the optimiser and the checkpoint logic are the real ones."""
+    import torch
+
+    tr = object.__new__(learned.Trainer)
+    tr.support, tr.per_cell, tr.device = 8, 16, torch.device("cpu")
+    tr.sky_case = lambda i: i
+    tr.loss = lambda table, i: ((table - 0.01 * (i % 5)) ** 2).mean()
+    return tr
+
+
+def test_training_resumes_from_a_checkpoint_as_if_uninterrupted(tmp_path):
+    """Six steps in one go against four steps (checkpoints at 2 and 4), then a fresh model
+    and optimiser resumed from the checkpoint for the last two: the losses and the final
+    parameters agree exactly."""
+    import torch
+
+    from paper_2301_06061_gb300 import learned
+
+    tr = _cpu_trainer(learned)
+    torch.manual_seed(5)
+    ref = learned.KernelMLP(8)
+    ref_hist = tr.train(ref, range(6), lr=1e-2)
+
+    ckpt = str(tmp_path / "train.pt")
+    torch.manual_seed(5)
+    first = learned.KernelMLP(8)
+    tr.train(first, range(4), lr=1e-2, checkpoint=ckpt, checkpoint_every=2)
+    torch.manual_seed(99)  # a different initialisation: everything must come from the file
+    resumed = learned.KernelMLP(8)
+    hist = tr.train(resumed, range(6), lr=1e-2, checkpoint=ckpt, checkpoint_every=2)
+
+    assert hist == ref_hist
+    for a, b in zip(ref.state_dict().values(), resumed.state_dict().values()):
+        assert torch.equal(a, b)
+    step, saved = learned.load_checkpoint(ckpt, learned.KernelMLP(8),
+                                          torch.optim.Adam(learned.KernelMLP(8).parameters()))
+    assert step == 6 and saved == ref_hist
+    assert not (tmp_path / "train.pt.tmp").exists()
