@@ -162,6 +162,28 @@ def test_w_range_from_data(wst):
     np.testing.assert_array_equal(k.cpu().numpy(), ko)
 
 
+def test_w_range_from_data_degenerate_single_w(wst):
+    """Every w equal and the range from the data: the range is empty, every visibility
+    goes to plane 0 (centre = that w), the other planes stay empty, and the image is the
+    oracle's (one plane with its screen)."""
+    u, v, _, vis = make_case(n=256, n_vis=3000, seed=77)
+    w = np.full(u.size, 37.5, np.float32)
+    cfg = wst.Config(n=256, fov=0.1, n_w=4)
+    plan = gpu_plan(wst, cfg, u, v, w, vis)
+    lo, hi = oracle.resolve_w_range(w, 0.0, 0.0)
+    s = plan.stats()
+    assert s["w_min"] == s["w_max"] == lo == hi == 37.5
+    k = torch.empty(u.size, dtype=torch.int32, device="cuda")
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(plan.handle, k, i0, j0)
+    oc = ocfg_for(cfg, lo, hi)
+    ko, _, _, _ = oracle.locate(oc, u, v, w, vis)
+    np.testing.assert_array_equal(k.cpu().numpy(), ko)
+    assert np.all(ko <= 0)  # plane 0 (a dropped visibility would read -1)
+    img = plan.image()
+    assert_image_parity(img[0].cpu().numpy(), oracle.image(oc, u, v, w, vis), oc)
+
+
 # ------------------------------------------------------------------------------------------
 # K-G: gridded planes
 # ------------------------------------------------------------------------------------------
