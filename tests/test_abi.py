@@ -64,3 +64,36 @@ def test_plan_create_rejects_bad_config_before_touching_the_device(lib):
         h = ctypes.c_void_p()
         rc = lib.wst_plan_create(ctypes.byref(cfg.c()), None, ctypes.byref(h))
         assert rc in (1, 5) and not h.value
+
+
+def _code_lines(path):
+    """Source lines without comments (C/C++ // and /* */, Python #) or docstring prose."""
+    text = open(path, encoding="utf-8").read()
+    if path.endswith((".cu", ".cuh", ".c", ".h")):
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        return [ln.split("//")[0] for ln in text.splitlines()]
+    text = re.sub(r'""".*?"""', "", text, flags=re.S)
+    return [ln.split("#")[0] for ln in text.splitlines()]
+
+
+def test_product_path_never_reaches_the_oracle():
+    """The package and its CUDA sources neither import, load nor build anything under
+    oracle/: the imager cannot fall back to the checker."""
+    pkg = os.path.join(ROOT, "paper_2301_06061_gb300")
+    files = [os.path.join(pkg, f) for f in os.listdir(pkg) if f.endswith(".py")]
+    csrc = os.path.join(pkg, "csrc")
+    files += [os.path.join(csrc, f) for f in os.listdir(csrc)]
+    offenders = [(f, ln.strip()) for f in files for ln in _code_lines(f)
+                 if re.search(r"\boracle\b|liboracle|wst_oracle", ln)]
+    assert not offenders, offenders
+
+
+def test_oracle_shares_no_code_with_the_cuda_library():
+    """The oracle's C source includes only the C library, and its Python side loads only
+    its own shared object."""
+    src = open(os.path.join(ROOT, "oracle", "wst_oracle.c")).read()
+    includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', src)
+    assert set(includes) <= {"complex.h", "math.h", "stdint.h", "stdlib.h", "string.h", "omp.h", "stdio.h"}, includes
+    for f in ("oracle.py", "__init__.py"):
+        code = "\n".join(_code_lines(os.path.join(ROOT, "oracle", f)))
+        assert "paper_2301_06061_gb300" not in code and "libwst" not in code and "csrc" not in code
