@@ -97,3 +97,11 @@ def test_oracle_shares_no_code_with_the_cuda_library():
     for f in ("oracle.py", "__init__.py"):
         code = "\n".join(_code_lines(os.path.join(ROOT, "oracle", f)))
         assert "paper_2301_06061_gb300" not in code and "libwst" not in code and "csrc" not in code
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    from paper_2301_06061_gb300 import wst
+
+    monkeypatch.setattr(wst, "_lib", None)  # as in a fresh process
+    with pytest.raises(RuntimeError, match="not found"):
+        wst.load_library(str(tmp_path / "libwst.so"))
