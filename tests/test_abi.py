@@ -105,3 +105,29 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(wst, "_lib", None)  # as in a fresh process
     with pytest.raises(RuntimeError, match="not found"):
         wst.load_library(str(tmp_path / "libwst.so"))
+
+
+@pytest.mark.parametrize("change,status", [
+    (dict(n=100), 5), (dict(n=32), 5), (dict(n=32768), 5), (dict(n=16384, oversample=2), 5),
+    (dict(oversample=3), 5), (dict(fov=0.0), 1), (dict(fov=float("nan")), 1), (dict(n_w=0), 1),
+    (dict(w_min=10.0, w_max=-10.0), 1), (dict(w_max=float("inf")), 1), (dict(support=1), 5),
+    (dict(support=17), 5), (dict(kernel=7), 1), (dict(kparam=-1.0), 1), (dict(kernel=2, ktable_len=1), 1),
+    (dict(flags=0x100), 1), (dict(batch=0), 1), (dict(planes_per_chunk=-1), 1),
+])
+def test_plan_create_rejects_invalid_configs_before_touching_the_device(lib, change, status):
+    """Configuration errors come back as WST_ERR_INVALID_ARG (1) or WST_ERR_UNSUPPORTED
+    (5) from host-side checks that run before any CUDA call (so this needs no GPU), and
+    no plan is returned."""
+    from paper_2301_06061_gb300 import wst
+
+    fields = dict(n=256, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0, support=7, kernel=0, kparam=0.875,
+                  ktable_len=0, flags=1, planes_per_chunk=0, batch=1, oversample=0)
+    fields.update(change)
+    cfg = wst.wst_config(*[fields[name] for name, _ in wst.wst_config._fields_])
+    h = ctypes.c_void_p(12345)
+    fn = lib.wst_plan_create
+    fn.argtypes = [ctypes.POINTER(wst.wst_config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    fn.restype = ctypes.c_int
+    assert fn(ctypes.byref(cfg), None, ctypes.byref(h)) == status
+    assert h.value is None
+    assert fn(ctypes.byref(cfg), None, None) == 1  # no output handle
