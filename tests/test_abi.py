@@ -131,3 +131,36 @@ def test_plan_create_rejects_invalid_configs_before_touching_the_device(lib, cha
     assert fn(ctypes.byref(cfg), None, ctypes.byref(h)) == status
     assert h.value is None
     assert fn(ctypes.byref(cfg), None, None) == 1  # no output handle
+
+
+def test_every_entry_point_rejects_a_null_plan_or_bad_sizes_without_a_device(lib):
+    """Argument errors are reported synchronously by host-side checks: a NULL plan, and
+    sizes no call accepts.  Nothing here reaches the GPU."""
+    from paper_2301_06061_gb300 import wst
+
+    L = wst.load_library()
+    calls = {
+        "wst_plan_set_stream": (None, None),
+        "wst_plan_workspace_bytes": (None, 10, None),
+        "wst_plan_set_workspace": (None, None, 0),
+        "wst_plan_set_kernel_table": (None, None),
+        "wst_plan_set_vis": (None, 0, None, None, None, None, None, None),
+        "wst_plan_set_vis_rows": (None, 0, None, 0, None, 1, None, None, None),
+        "wst_grid": (None, 0, 1, None),
+        "wst_fft_correct": (None, 0, 1, None, None),
+        "wst_correct": (None, None),
+        "wst_image": (None, None, 0),
+        "wst_degrid": (None, None, None, 0),
+        "wst_kernel_grad": (None, None, None, 0),
+        "wst_vis_cells": (None, None, None, None),
+        "wst_get_stats": (None, None),
+        "wst_dft": (1, None, None, None, None, None, 1, 0.1, 1, None, None, None, None),  # n < 2
+        "wst_dft_noalloc": (1, None, None, None, None, None, 1, 0.1, 1, None, None, None, None),
+        "wst_predict_points": (-1, None, None, None, 1, None, None, None, None, None),  # n_vis < 0
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == 1, name  # WST_ERR_INVALID_ARG
+    L.wst_plan_destroy(None)  # a no-op
+    assert L.wst_last_error(None) == b""
+    for s in range(7):
+        assert L.wst_status_string(s)
