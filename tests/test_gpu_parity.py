@@ -324,6 +324,28 @@ def test_image_from_pinned_host_buffers_in_place(wst, n):
     assert rel_err(host_img[0].numpy(), dev_img) < 1e-6
 
 
+def test_set_vis_without_or_with_a_short_workspace_is_oom(wst):
+    """WST_ERR_OOM (2) from the host-side check, before any launch, when no workspace is
+    set or it is one alignment unit smaller than wst_plan_workspace_bytes asks for; the
+    exact size is accepted (a view of a larger buffer, so nothing past it is unmapped)."""
+    u, v, w, vis = make_case(n=256, n_vis=1000, seed=5)
+    cfg = wst.Config(n=256, fov=0.1, n_w=2, w_min=-200.0, w_max=200.0)
+    plan = wst.Plan(cfg)
+    args = (dev(u), dev(v), dev(w), dev(vis))
+    with pytest.raises(wst.WstError) as e:
+        wst.wst_plan_set_vis(plan.handle, *args)
+    assert e.value.status == 2
+    need = wst.wst_plan_workspace_bytes(plan.handle, u.size)
+    buf = torch.empty(need + 4096, dtype=torch.uint8, device="cuda")
+    wst.wst_plan_set_workspace(plan.handle, buf[:need - 256])
+    with pytest.raises(wst.WstError) as e:
+        wst.wst_plan_set_vis(plan.handle, *args)
+    assert e.value.status == 2
+    wst.wst_plan_set_workspace(plan.handle, buf[:need])
+    wst.wst_plan_set_vis(plan.handle, *args)
+    assert plan.stats()["n_kept"] == u.size
+
+
 def test_pageable_or_foreign_host_tensors_rejected_by_binding(wst):
     with pytest.raises(ValueError):
         wst._ptr(torch.zeros(4), True)  # not page-locked
