@@ -28,3 +28,22 @@ def test_step_roofline_sums_the_stages_and_states_the_all_resident_floor():
     assert r["achieved"] == pytest.approx(total / 63.8e-3 / 1e9, abs=0.1)
     assert r["frac"] == pytest.approx(total / 63.8e-3 / 1e9 / 6769.4, abs=1e-4)
     assert r["frac_of_all_resident_floor"] == pytest.approx(129 * S / 63.8e-3 / 1e9 / 6769.4, abs=1e-4)
+
+
+def test_synthetic_workloads_follow_their_stated_recipes():
+    """The shapes the bench lines and the design notes quote: the array workload is
+    60 stations (1770 baselines) x 144 dumps x 16 channels; the benchmark's 1e8
+    visibilities need 35 dumps of 300 stations (44,850 baselines) x 64 channels; the
+    64 batched images hold 1e5 to 2e6 visibilities each, 37.7M in all."""
+    from paper_2301_06061_gb300 import synth
+
+    a = synth.array()
+    assert a.n_vis == 1770 * 144 * 16 == 4_078_080 and (a.n, a.n_w, a.fov) == (4096, 32, 0.2)
+    assert a.rows_m.shape == (1770 * 144, 3) and a.chan_scale.size == 16
+    assert -(-100_000_000 // (44_850 * 64)) == 35
+    small = synth.large(n_vis=3_000_000)
+    assert small.n_vis == 3_000_000 and small.rows_m.shape[1] == 3 and small.chan_scale.size == 64
+    assert small.rows_m.shape[0] % 44_850 == 0
+    c = synth.batched_counts()
+    assert c.size == 64 and c.min() >= 100_000 and c.max() <= 2_000_000
+    assert round(c.sum() / 1e6, 1) == 37.7
