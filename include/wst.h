@@ -304,8 +304,12 @@ wst_status wst_predict_points(int64_t n_vis, const float *u, const float *v, con
  *
  * Limits and rules:
  *   - n_pix <= WST_DFT_NOALLOC_MAX_PIX, else WST_ERR_UNSUPPORTED and nothing runs.
- *   - The first call on each device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *   - The array's device address belongs to a CUDA context (a device's primary
+ *     context, a context the caller made current with the driver API, the primary
+ *     context re-created after cudaDeviceReset).  The first call in each context
+ *     looks it up (cudaGetSymbolAddress, with that context current) and remembers
+ *     it under the driver's unique context id; later calls in that context reuse
+ *     it.  Make that first call before any stream capture.
  *   - Every call on a device shares the one array: calls whose GPU work overlaps
  *     (other streams, other host threads) race and corrupt each other's sums.
  *     Serialise them, e.g. on one stream.
