@@ -142,6 +142,18 @@ void wst_plan_destroy(wst_plan plan);
 wst_status wst_plan_set_stream(wst_plan plan, void *cuda_stream);
 
 /*
+ * Time limit, in nanoseconds, of the plan's device-side waits for data: the row FFT of
+ * a 16384-point grid (wst_fft_correct) waits on each row's bulk copy into shared
+ * memory.  Default 2e9 (2 s); at most 6e10.  On expiry the kernel sets the device error
+ * word to WST_ERR_TIMEOUT (read by wst_get_stats), waits -- with the default limit,
+ * whatever this setting -- for the copy it has in flight, and returns; the plan stays
+ * usable (the word is cleared by the next wst_plan_set_vis).  0 makes every such wait
+ * expire at once without looking: it exercises that failure path on purpose (tests of
+ * the caller's error handling).  Not in the paper.  Errors: INVALID_ARG.
+ */
+wst_status wst_plan_set_wait_limit(wst_plan plan, uint64_t wait_ns);
+
+/*
  * Bytes of device workspace needed for `n_vis` visibilities (sort buffers,
  * bucket offsets, one chunk of planes, compensation image).  Host-only call.
  */

@@ -91,10 +91,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+// Wait for the phase with a time limit; a zero limit expires at once without looking
+// (the plan's failure-path test setting, wst_plan_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, unsigned long long limit_ns) {
+  if (limit_ns == 0) return false;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(mbar, phase)) {
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -117,7 +120,8 @@ __device__ __forceinline__ void tma_load_row(uint32_t dst_smem, const float2 *sr
 
 template <int N, int DIR, bool PRESIGN, bool POSTSIGN>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS, 1)
-k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long long *err) {
+k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long long *err,
+           unsigned long long wait_ns) {
   using C = RowCfg<N>;
   static_assert(C::RPC == 1, "one row per CTA");
   constexpr int EPT = C::EPT, TPR = C::TPR;
@@ -141,11 +145,13 @@ k_rows_tma(float2 *__restrict__ planes, int64_t total_rows, Tw tw, unsigned long
   for (; row < total_rows; row += gridDim.x) {
     // one warp polls the barrier; the others wait at the CTA barrier without issuing
     bool ok = true;
-    if (threadIdx.x < 32) ok = mbar_wait_bounded(mbar, phase);
+    if (threadIdx.x < 32) ok = mbar_wait_bounded(mbar, phase, wait_ns);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, (unsigned long long)WST_ERR_TIMEOUT);
-        mbar_wait_bounded(mbar, phase);  // let a late copy into our buffer land, also bounded
+        // let the copy in flight into our buffer land before the CTA exits: bounded, with
+        // the full limit whatever the plan's setting
+        mbar_wait_bounded(mbar, phase, kWaitLimitNs);
       }
       __syncthreads();
       return;
@@ -840,7 +846,7 @@ static cudaError_t launch_rows(wst_plan_s *p, float2 *planes, int nplanes) {
     if (e != cudaSuccess) return e;
     const int64_t rows = (int64_t)nplanes * N;
     const int grid = (int)(rows < sms ? rows : sms);
-    kern<<<grid, C::THREADS, smem, p->stream>>>(planes, rows, tw_of(p), p->W_.counters + CNT_ERROR);
+    kern<<<grid, C::THREADS, smem, p->stream>>>(planes, rows, tw_of(p), p->W_.counters + CNT_ERROR, p->wait_ns);
   } else {
     auto kern = k_rows<N, DIR, PRE, POST>;
     if (smem > 48 * 1024) {

@@ -242,6 +242,13 @@ wst_status wst_plan_set_stream(wst_plan p, void *cuda_stream) {
   return WST_OK;
 }
 
+wst_status wst_plan_set_wait_limit(wst_plan p, uint64_t wait_ns) {
+  if (!p) return WST_ERR_INVALID_ARG;
+  if (wait_ns > 60000000000ull) return fail(p, WST_ERR_INVALID_ARG, "wait limit above 60 s");
+  p->wait_ns = wait_ns;
+  return WST_OK;
+}
+
 wst_status wst_plan_workspace_bytes(wst_plan p, int64_t n_vis, size_t *bytes) {
   if (!p || !bytes || n_vis < 0 || n_vis >= (int64_t)0xFFFFFFFFu) return WST_ERR_INVALID_ARG;
   *bytes = layout_for(p, n_vis).total;

@@ -119,6 +119,9 @@ struct wst_plan_s {
   double *wcentre_d = nullptr;  // per global plane: centre w_k (FP64)
   float2 *dwff = nullptr;    // per image: plane spacing dw as float-float
   bool table_set = false;
+  // limit of the device-side waits for data (the row kernel's bulk copies), nanoseconds;
+  // 0 = expire at once (failure-path testing, wst_plan_set_wait_limit)
+  unsigned long long wait_ns = 2000000000ull;
   // workspace
   char *ws = nullptr;
   size_t ws_bytes = 0;

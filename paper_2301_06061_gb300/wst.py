@@ -28,7 +28,7 @@ WST_NO_CORRECTION = 0x1
 
 EXPORTED = [
     "wst_version", "wst_status_string", "wst_plan_create", "wst_plan_destroy", "wst_plan_set_stream",
-    "wst_plan_workspace_bytes", "wst_plan_set_workspace", "wst_plan_set_kernel_table",
+    "wst_plan_set_wait_limit", "wst_plan_workspace_bytes", "wst_plan_set_workspace", "wst_plan_set_kernel_table",
     "wst_plan_set_vis", "wst_plan_set_vis_rows", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_degrid",
     "wst_kernel_grad", "wst_vis_cells", "wst_get_stats", "wst_last_error", "wst_dft",
     "wst_predict_points", "wst_dft_noalloc",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "wst_plan_create": ([ctypes.POINTER(wst_config), P, ctypes.POINTER(P)], ctypes.c_int),
             "wst_plan_destroy": ([P], None),
             "wst_plan_set_stream": ([P, P], ctypes.c_int),
+            "wst_plan_set_wait_limit": ([P, ctypes.c_uint64], ctypes.c_int),
             "wst_plan_workspace_bytes": ([P, I64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
             "wst_plan_set_workspace": ([P, P, ctypes.c_size_t], ctypes.c_int),
             "wst_plan_set_kernel_table": ([P, P], ctypes.c_int),
@@ -175,6 +176,10 @@ def wst_plan_destroy(plan) -> None:
 
 def wst_plan_set_stream(plan, stream=None) -> None:
     _check(load_library().wst_plan_set_stream(plan, _stream(stream)), "wst_plan_set_stream", plan)
+
+
+def wst_plan_set_wait_limit(plan, wait_ns: int) -> None:
+    _check(load_library().wst_plan_set_wait_limit(plan, int(wait_ns)), "wst_plan_set_wait_limit", plan)
 
 
 def wst_plan_workspace_bytes(plan, n_vis: int) -> int:
@@ -338,6 +343,9 @@ class Plan:
             self.handle = wst_plan_create(cfg.c())
         self.ws = None
         self.n_vis = 0
+        # bumped by every call that rebinds the visibilities or the kernel table, so that
+        # a caller holding work from an earlier binding can tell the plan has moved on
+        self.generation = 0
 
     def close(self):
         if self.handle is not None:
@@ -358,18 +366,21 @@ class Plan:
 
     def set_kernel_table(self, table: torch.Tensor):
         wst_plan_set_kernel_table(self.handle, table.contiguous())
+        self.generation += 1
 
     def set_vis(self, u, v, w, vis, weight=None, batch_offsets=None):
         self.ensure_workspace(u.numel())
         wst_plan_stream(self.handle)
         wst_plan_set_vis(self.handle, u, v, w, vis, weight, batch_offsets)
         self.n_vis = u.numel()
+        self.generation += 1
 
     def set_vis_rows(self, uvw_m, chan_scale, vis, weight=None, batch_offsets=None):
         self.ensure_workspace(vis.numel())
         wst_plan_stream(self.handle)
         wst_plan_set_vis_rows(self.handle, uvw_m, chan_scale, vis, weight, batch_offsets)
         self.n_vis = vis.numel()
+        self.generation += 1
 
     def image(self, out=None, flags: int = 0) -> torch.Tensor:
         c = self.cfg

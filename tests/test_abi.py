@@ -141,6 +141,7 @@ def test_every_entry_point_rejects_a_null_plan_or_bad_sizes_without_a_device(lib
     L = wst.load_library()
     calls = {
         "wst_plan_set_stream": (None, None),
+        "wst_plan_set_wait_limit": (None, 0),
         "wst_plan_workspace_bytes": (None, 10, None),
         "wst_plan_set_workspace": (None, None, 0),
         "wst_plan_set_kernel_table": (None, None),
