@@ -158,3 +158,85 @@ def test_predict_matches_oracle(wst):
     wst.wst_predict_points(dev(u), dev(v), dev(w), dev(sky.l), dev(sky.m), dev(sky.flux), out)
     ref = oracle.predict_points(u, v, w, sky.l, sky.m, sky.flux)
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-5 * np.abs(sky.flux).sum()
+
+
+def test_autograd_two_forwards_on_one_plan_before_backward(wst):
+    """Each backward differentiates its own forward, also when a second forward has
+    rebound the plan in between (the binding is restored from the saved inputs)."""
+    from paper_2301_06061_gb300 import autograd
+
+    n = 128
+    plan = wst.Plan(wst.Config(n=n, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0))
+    ocfg = OracleConfig(n, 0.1, 4, -200.0, 200.0, 7)
+    cases, outs = [], []
+    for seed in (21, 22):
+        u, v, w, vis, wt, rng = case(n=n, seed=seed, n_vis=1500 + seed)
+        y = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        V = dev(vis).requires_grad_(True)
+        D = autograd.image(V, plan, dev(u), dev(v), dev(w), dev(wt))
+        cases.append((u, v, w, vis, wt, y, V))
+        outs.append(torch.real(torch.sum(torch.conj(dev(y.astype(np.complex64))) * D[0])))
+    for (u, v, w, vis, wt, y, V), loss in zip(cases, outs):  # the first forward's backward first
+        loss.backward()
+        ref = oracle.degrid(ocfg, u, v, w, vis, y, wt)
+        assert rel_err(V.grad.cpu().numpy(), ref) < TOL
+
+
+def test_kernel_autograd_two_forwards_on_one_plan_before_backward(wst):
+    from paper_2301_06061_gb300 import autograd
+
+    n, W = 128, 8
+    L = W * 32 + 1
+    xs = np.linspace(-W / 2, W / 2, L)
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0, support=W, kernel=wst.WST_KERNEL_TABLE,
+                     ktable_len=L, kparam=0.0)
+    plan = wst.Plan(cfg)
+    cases, outs = [], []
+    for seed, wiggle in ((31, 0.05), (32, -0.08)):
+        u, v, w, vis, wt, rng = case(n=n, n_vis=1200, seed=seed)
+        tab = (np.exp(-xs**2 / (2 * 0.925**2)) * (1 + wiggle * np.sin(xs))).astype(np.float32)
+        T = dev(tab).requires_grad_(True)
+        U = autograd.kernel_image(T, plan, dev(u), dev(v), dev(w), dev(vis), dev(wt))
+        dU = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+        cases.append((u, v, w, vis, wt, tab, dU, T))
+        outs.append(torch.real(torch.sum(torch.conj(dev(dU)) * U[0])))
+    for (u, v, w, vis, wt, tab, dU, T), loss in zip(cases, outs):
+        loss.backward()
+        ocfg = OracleConfig(n, 0.1, 3, -200.0, 200.0, W, "table", 0.0, tab.astype(np.float64))
+        ref = oracle.kernel_grad(ocfg, u, v, w, vis, dU, wt)
+        assert np.abs(T.grad.cpu().numpy() - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def test_degrid_matches_fp64_central_differences_of_the_oracle_image(wst):
+    """wst_degrid against central differences (eps = 1e-3) of the FP64 oracle's image on
+    the tiny workload's geometry (256^2, FoV 0.1, 8 planes over [-200, 200], Gaussian
+    W = 7).  The image is linear in the visibilities, so the differences are the exact
+    derivatives up to FP64 rounding: for L(V) = Re sum conj(y) D(V), dL/dRe V_j =
+    Re (A^H y)_j and dL/dIm V_j = Im (A^H y)_j."""
+    n, n_w, fov, eps = 256, 8, 0.1, 1e-3
+    u, v, w, vis, wt, rng = case(n=n, n_vis=2000, seed=41, fov=fov)
+    ocfg = OracleConfig(n, fov, n_w, -200.0, 200.0, 7)
+    y = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+
+    def loss(values):
+        return float(np.real(np.vdot(y, oracle.image(ocfg, u, v, w, values, wt))))
+
+    picks = rng.choice(2000, 12, replace=False)
+    fd = np.zeros(picks.size, np.complex128)
+    for i, j in enumerate(picks):
+        parts = []
+        for direction in (1.0, 1j):
+            # the oracle reads complex64 values: the step is what V_j +/- eps round to
+            lp, lm = vis.copy(), vis.copy()
+            lp[j] = np.complex64(np.complex128(vis[j]) + direction * eps)
+            lm[j] = np.complex64(np.complex128(vis[j]) - direction * eps)
+            step = ((np.complex128(lp[j]) - np.complex128(lm[j])) / direction).real
+            parts.append((loss(lp) - loss(lm)) / step)
+        fd[i] = parts[0] + 1j * parts[1]
+    # the oracle's own adjoint agrees with its differences (FP64 rounding of L / eps)
+    ref = oracle.degrid(ocfg, u, v, w, vis, y, wt)[picks]
+    assert np.abs(fd - ref).max() < 1e-7 * np.abs(ref).max()
+    plan = wst.Plan(wst.Config(n=n, fov=fov, n_w=n_w, w_min=-200.0, w_max=200.0))
+    plan.set_vis(dev(u), dev(v), dev(w), dev(vis), dev(wt))
+    got = plan.degrid(dev(y.astype(np.complex64)[None])).cpu().numpy()[picks].astype(np.complex128)
+    assert np.abs(got - fd).max() < TOL * np.abs(fd).max()
