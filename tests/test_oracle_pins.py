@@ -206,6 +206,77 @@ def test_locate_exact_rules():
         assert int(k[j]) == kk
 
 
+def _plane_boundary_cases(w_min, w_max, n_w):
+    """FP32 w on, and 1 or 2 FP32 steps either side of, every interior plane boundary
+    w_min + k (w_max - w_min) / n_w (the FP32 values nearest to each boundary)."""
+    F = Fraction
+    ws = []
+    for k in range(1, n_w):
+        b = F(w_min) + k * (F(w_max) - F(w_min)) / n_w
+        c = np.float32(float(b))
+        ws += [c, np.nextafter(c, np.float32(np.inf)), np.nextafter(c, np.float32(-np.inf))]
+        ws += [np.nextafter(ws[-2], np.float32(np.inf)), np.nextafter(ws[-1], np.float32(-np.inf))]
+    return np.array(ws, np.float32)
+
+
+@pytest.mark.parametrize("w_min,w_max,n_w,n_down", [
+    (-256.0, 256.0, 32, 0),         # dyadic N_w / range: the product is exact
+    (-200.0, 200.0, 8, 0),          # the tiny workload's planes; N_w / range rounds up in FP64
+    (-6547.25, 6728.5, 32, 0),      # a range like the benchmark's: dw dyadic, N_w / range rounds down
+    (-1000.0, 2000.0, 3, 0),        # dw = 1000: boundaries exact in FP32, N_w / range rounds up
+    (-0.75, 6.0, 27, 0),            # N_w / range = 4: dyadic again
+    (-3.3333332538604736, 6.6666669845581055, 48, 1),  # FP32 end points; rounds down, one hit goes down
+])
+def test_locate_plane_rule_at_exact_boundaries(w_min, w_max, n_w, n_down):
+    """The plane rule k = floor(fl(fl(w - w_min) * fl(N_w / (w_max - w_min)))) (closest
+    plane, section 2; FP64, one product per visibility) against exact rational arithmetic
+    q = (w - w_min) N_w / (w_max - w_min), k_exact = floor(q), with w on, and 1-2 FP32
+    steps from, each boundary.  Three FP64 roundings (difference, scale, product) move
+    q by at most 2^-50 |q|, so:
+      * where q is farther than that from an integer, the exact plane is taken;
+      * where q is within that of an integer m but not equal to it (here: the boundary at
+        w = 0, whose FP32 neighbours are subnormal, so fl(w - w_min) = -w_min), the
+        visibility goes to m - 1 or m -- both planes are closest to within FP64 rounding;
+      * where q is exactly an integer m (w exactly on a boundary), the visibility goes to
+        the upper plane m when fl(N_w / range) >= N_w / range (a dyadic or rounded-up
+        scale), and may go to m - 1 only when the scale rounded down.
+    The GPU sort takes the same decision as this rule, bit for bit."""
+    F = Fraction
+    w = _plane_boundary_cases(w_min, w_max, n_w)
+    cfg = OracleConfig(64, 0.1, n_w, w_min, w_max, 7)
+    z = np.zeros(w.size, np.float32)
+    k, _, _, st = oracle.locate(cfg, z, z, w, np.ones(w.size, np.complex64))
+    assert np.all(st == 0)
+    scale_exact = F(n_w) / (F(w_max) - F(w_min))
+    scale_rounded_down = F(n_w / (w_max - w_min)) < scale_exact
+    hits = near = down = 0
+    for j in range(w.size):
+        q = (F(float(w[j])) - F(w_min)) * scale_exact
+        m = round(q)
+        got = int(k[j])
+        if q == m:  # exactly on a boundary
+            hits += 1
+            if scale_rounded_down:
+                assert got in (m - 1, m), (w[j], got, m)
+                down += got == m - 1
+            else:
+                assert got == min(m, n_w - 1), (w[j], got, m)
+        elif abs(q - m) <= F(1, 2**50) * max(abs(q), 1):
+            near += 1
+            assert got in (m - 1, m), (w[j], got, m)
+        else:
+            assert got == min(max(math.floor(q), 0), n_w - 1), (w[j], got, q)
+    # the dyadic configurations and the exact-dw one really put w on the boundaries
+    if (w_min, n_w) in ((-256.0, 32), (-1000.0, 3), (-0.75, 27)):
+        assert hits == n_w - 1
+    # a boundary at w = 0 has subnormal neighbours: four cases within FP64 rounding
+    if (w_min, n_w) in ((-256.0, 32), (-200.0, 8), (-1000.0, 3), (-0.75, 27)):
+        assert near == 4
+    # exact hits that the rounded-down scale sends to the lower plane (w = -0.2083331794
+    # on the boundary of planes 14 and 15 of the last configuration)
+    assert down == n_down
+
+
 def test_plane_centres_cell_centred():
     cfg = OracleConfig(64, 0.1, 8, -200.0, 200.0, 7)
     assert [oracle.plane_centre(cfg, k) for k in range(8)] == [-175, -125, -75, -25, 25, 75, 125, 175]
