@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="planes per chunk (0 = all planes resident)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison of the transform stage")
     ap.add_argument("--dft-pixels", type=int, default=64)
     ap.add_argument("--n-w", type=int, default=0, help="override the number of w-planes (profiling cases)")
     ap.add_argument("--vis-frac", type=float, default=1.0, help="keep this fraction of the visibilities")
@@ -341,38 +342,63 @@ def profiled_traffic(kernel_stage: str, workload: str, launch_scale: float):
 # CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
 # ------------------------------------------------------------------------------------------
 
+ORACLE_SAMPLE_MAX_VIS = 4_000_000
+
+
 def oracle_sample(work, vis, plane: int):
-    """One w-plane of the workload with its visibilities, as an n_w = 1 oracle problem."""
+    """One w-plane of the workload with (a seeded subset of at most 4M of) its
+    visibilities, as an n_w = 1 oracle problem on the full image."""
     import oracle
 
     lo, hi = oracle.resolve_w_range(work.w, work.w_min, work.w_max) if work.batch_offsets is None else (0, 0)
     full = oracle.OracleConfig(work.n, work.fov, work.n_w, lo, hi, work.support, "gauss", 0.875)
     k, _, _, st = oracle.locate(full, work.u, work.v, work.w, vis)
     sel = np.nonzero((st == 0) & (k == plane))[0]
+    if sel.size > ORACLE_SAMPLE_MAX_VIS:
+        sel = np.sort(np.random.default_rng(2301).choice(sel, ORACLE_SAMPLE_MAX_VIS, replace=False))
     dw = (hi - lo) / work.n_w
     cfg = oracle.OracleConfig(work.n, work.fov, 1, lo + plane * dw, lo + (plane + 1) * dw, work.support,
                               "gauss", 0.875)
     return cfg, work.u[sel], work.v[sel], work.w[sel], vis[sel]
 
 
+def oracle_job_seconds(t_grid: float, t_image: float, n_sample: int, n_vis: int, n_w: int) -> float:
+    """The whole job's oracle time from one sample plane: gridding scales with the
+    visibilities, the transform, screen and plane sum with the planes.  The sample's
+    image time t_image = t_grid + t_rest (one plane's FFT, screen, sum and the final
+    correction), so job = (n_vis / n_sample) t_grid + n_w t_rest (which bills the
+    correction, an elementwise pass, once per plane: an upper bound)."""
+    t_rest = max(t_image - t_grid, 0.0)
+    return (n_vis / max(n_sample, 1)) * t_grid + n_w * t_rest
+
+
 def time_oracle_sample(work, vis, repeats: int = 1):
-    """Seconds per full job, extrapolated from one plane of the single-image workloads;
-    also returns the sample and the oracle's image of it."""
+    """Seconds per full job, extrapolated from one plane of the single-image workloads by
+    oracle_job_seconds; also the seconds this sample took, a description, the thread
+    count, and the sample with the oracle's image of it."""
     import oracle
 
     plane = work.n_w // 2
     cfg, u, v, w, vv = oracle_sample(work, vis, plane)
-    times = []
+    tg, ti = [], []
     ref = None
     for _ in range(repeats):
         t0 = time.perf_counter()
+        oracle.grid(cfg, u, v, w, vv)
+        t1 = time.perf_counter()
         ref = oracle.image(cfg, u, v, w, vv)
-        times.append(time.perf_counter() - t0)
-    t_plane = statistics.median(times)
-    job_s = t_plane * work.n_w  # the job is n_w such planes (plus their share of visibilities)
-    sample = (f"w-plane {plane} of {work.n_w} ({u.size} of {work.n_vis} visibilities, {work.n}^2 FP64 grid, "
-              f"FFT, screen, correction); time x {work.n_w} planes")
-    return job_s, sample, oracle.num_threads(), (cfg, u, v, w, vv, ref)
+        t2 = time.perf_counter()
+        tg.append(t1 - t0)
+        ti.append(t2 - t1)
+    t_grid, t_image = statistics.median(tg), statistics.median(ti)
+    job_s = oracle_job_seconds(t_grid, t_image, u.size, work.n_vis, work.n_w)
+    sample = (f"w-plane {plane} of {work.n_w}: {u.size} of its visibilities (of {work.n_vis}), {work.n}^2 FP64 "
+              f"grid, FFT, screen, correction; gridding alone {t_grid:.2f} s, the plane's image {t_image:.2f} s")
+    extrap = {"formula": "job_s = (n_vis / n_sample) * t_grid + n_w * (t_image - t_grid)",
+              "n_vis": work.n_vis, "n_sample": int(u.size), "n_w": work.n_w, "t_grid_s": round(t_grid, 4),
+              "t_image_s": round(t_image, 4), "job_s": round(job_s, 3)}
+    measured_s = (sum(tg) + sum(ti)) / repeats  # seconds this sample took per repeat
+    return job_s, sample, oracle.num_threads(), (cfg, u, v, w, vv, ref), extrap, measured_s
 
 
 def oracle_parity(torch, wst, dev, sample):
@@ -394,6 +420,65 @@ def oracle_parity(torch, wst, dev, sample):
     return {"sample": f"w-plane slab of the workload, {u.size} visibilities, {n}^2, full image",
             "central_half_max_err_rel_peak": float(err[q, q].max() / np.abs(ref[q, q]).max()),
             "max_err_rel_peak": float(err.max() / peak)}
+
+
+# ------------------------------------------------------------------------------------------
+# cuFFT as a yardstick for the transform stage (comparison only, never on the product path)
+# ------------------------------------------------------------------------------------------
+
+def centred_fft_cufft(torch, planes):
+    """The centred, unnormalised, positive-exponent 2D transform of Eq. 2 by cuFFT
+    (torch.fft): F = (-1)^(a+b) IFFT2((-1)^(p+q) g) without the 1/N^2 (N divisible by 4)."""
+    n = planes.shape[-1]
+    idx = torch.arange(n, device=planes.device)
+    sign = (1 - 2 * ((idx[:, None] + idx[None, :]) & 1)).to(planes.real.dtype)
+    return torch.fft.ifft2(planes * sign, norm="forward") * sign
+
+
+def cufft_compare(torch, wst, plan, work, dev, stage_ms_per_plane: dict, peak: float, n_planes: int = 2):
+    """Planes of the benchmark (wst_grid) transformed by cuFFT and by this library's
+    transform stage, timed and compared.  This library's plain transform comes from
+    wst_fft_correct on a one-plane plan whose plane centre is w = 0 (screen exactly 1)."""
+    n = work.n
+    p0 = work.n_w // 2
+    g = torch.empty((n_planes, n, n), dtype=torch.complex64, device=dev)
+    wst.wst_grid(plan.handle, p0, p0 + n_planes, g)
+    stream = torch.cuda.current_stream(dev)
+    out = centred_fft_cufft(torch, g)  # warm-up (plans cuFFT)
+    del out
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        out = torch.fft.ifft2(g, norm="forward")  # the transform alone (no centring signs)
+        del out
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plane = e0.elapsed_time(e1) / reps / n_planes
+    S = 8.0 * n * n
+    ref = centred_fft_cufft(torch, g[:1])[0]
+    zero = wst.Plan(wst.Config(n=n, fov=work.fov, n_w=1, w_min=-1.0, w_max=1.0, flags=wst.WST_FLAG_KAHAN),
+                    device=dev)
+    e = torch.empty(0, dtype=torch.float32, device=dev)
+    zero.set_vis(e, e, e, torch.empty(0, dtype=torch.complex64, device=dev))
+    ours = torch.zeros((1, n, n), dtype=torch.complex64, device=dev)
+    wst.wst_fft_correct(zero.handle, 0, 1, g[:1].contiguous(), ours)
+    diff = float((ours[0] - ref).abs().max() / ref.abs().max())
+    zero.close()
+    del g, ref, ours
+    ours_ms = sum(stage_ms_per_plane.values())
+    return {"what": "cuFFT (torch.fft.ifft2, c2c FP32, out of place) on planes of this workload, against this "
+                    "library's transform stage (row FFT inside the gridding kernel, column stages A and B)",
+            "n": n, "planes_timed": n_planes, "cufft_ms_per_plane": round(ms_plane, 4),
+            "cufft_gbs_on_4S": round(4 * S / (ms_plane * 1e-3) / 1e9, 1),
+            "cufft_frac_of_hbm_on_4S": round(4 * S / (ms_plane * 1e-3) / 1e9 / peak, 4),
+            "ours_ms_per_plane": {k: round(v, 4) for k, v in stage_ms_per_plane.items()},
+            "ours_total_ms_per_plane": round(ours_ms, 4),
+            "ours_note": "the row pass is fused with gridding and column stage B with the phase screen and the "
+                         "plane sum, so these include work cuFFT does not do",
+            "max_diff_rel_peak": diff,
+            "diff_of": "centred transform of one plane: wst_fft_correct on a one-plane plan with w_k = 0 vs cuFFT"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -507,6 +592,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     roofline["step"] = step_roofline({k: v / args.steps for k, v in stages.items()}, work.n, planes,
                                      st["n_chunks"], batch, st["n_kept"], n_vis, osf, ms_step, peak)
 
+    cufft = None
+    if batch == 1 and not args.no_cufft:
+        per_plane = {k: stages[k] / args.steps / planes for k in ("grid", "cols_a", "cols_b")}
+        cufft = cufft_compare(torch, wst, plan, work, dev, per_plane, peak)
+
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -581,12 +671,34 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         acc = accuracy_block(torch, wst, work, st, d_u, d_v, d_w, d_vis, img, dev, args.dft_pixels,
                              args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold,
                              max(1, args.oversample))
+        if not args.snap_w and not args.wfold:
+            # the same visibilities with every w moved to its plane's centre: the error
+            # against the direct transform is then the (u, v) kernel's alone
+            lo, hi = float(st["w_min"]), float(st["w_max"])
+            k = torch.clamp(torch.floor((d_w.double() - lo) * (work.n_w / (hi - lo))), 0, work.n_w - 1)
+            d_ws = (lo + (k + 0.5) * (hi - lo) / work.n_w).float()
+            plan.close()  # its workspace is no longer needed
+            plan = wst.Plan(wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=lo, w_max=hi,
+                                       flags=wst.WST_FLAG_KAHAN, planes_per_chunk=min(8, work.n_w),
+                                       oversample=args.oversample, **kcfg), device=dev)
+            if table is not None:
+                plan.set_kernel_table(table)
+            plan.set_vis(d_u, d_v, d_ws, d_vis)
+            plan.image(out=img)
+            snapped = accuracy_block(torch, wst, work, plan.stats(), d_u, d_v, d_ws, d_vis, img, dev,
+                                     args.dft_pixels, args.kernel, cfg.support, sigma,
+                                     None if table is None else tab_np, False, max(1, args.oversample))
+            acc["w_snapped"] = {k2: snapped[k2] for k2 in (
+                "max_err_rel_peak", "central_max_err_rel_peak", "inner3q_max_err_rel_peak",
+                "inner3q_rms_err_rel_peak", "max_err_over_bound", "bound_rel_peak", "kernel_error_max")}
+            acc["w_snapped"]["what"] = ("every w moved to its plane's centre (same planes, same pixels): the "
+                                        "kernel's (u, v) error alone, without the nearest-plane phase error")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and batch == 1:
-        job_s, sample, cores, osample = time_oracle_sample(work, vis_np)
+        job_s, sample, cores, osample, extrap, _ = time_oracle_sample(work, vis_np)
         cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "extrapolation": extrap}
         if args.kernel == "gauss" and not args.snap_w and not args.wfold and args.oversample < 2:
             cpu["parity_vs_oracle"] = oracle_parity(torch, wst, dev, osample)
 
@@ -603,7 +715,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "cufft_compare": cufft,
             "ggpas": {"step": round(n_vis * cfg.support ** 2 / (ms_step * 1e-3) / 1e9, 2),
                       "grid_kernel": round(n_vis * cfg.support ** 2 / (stages["grid"] / args.steps * 1e-3) / 1e9, 2),
                       "note": "grid-point additions per second (N_vis W^2 / time); the grid kernel also "
@@ -628,19 +740,24 @@ def run_reference(args, rank: int, world: int):
     import oracle
 
     oracle.build()
-    times = []
-    sample = cores = None
+    jobs, measured = [], []
+    sample = cores = extrap = None
     for i in range(args.warmup + args.steps):
-        job_s, sample, cores, _ = time_oracle_sample(work, vis_np)
+        job_s, sample, cores, _, extrap, step_s = time_oracle_sample(work, vis_np)
         if i >= args.warmup:
-            times.append(job_s)
-    job_s = statistics.mean(times)
+            jobs.append(job_s)
+            measured.append(step_s)
+    job_s = statistics.mean(jobs)
     value = work.n_vis / job_s / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mvis/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(job_s * 1e3, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(measured) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
                        "n_vis": work.n_vis},
+            "step": "one timed sample of the job (gridding of the sample's visibilities, then the sample plane's "
+                    "image); ms_per_step is its measured time, value the whole job's throughput extrapolated "
+                    "from it (extrapolated_job_ms, extrapolation)",
+            "extrapolated_job_ms": round(job_s * 1e3, 1), "extrapolation": extrap,
             "cpu_baseline": {"value": round(value, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "Mvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

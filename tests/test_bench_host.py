@@ -47,3 +47,13 @@ def test_synthetic_workloads_follow_their_stated_recipes():
     c = synth.batched_counts()
     assert c.size == 64 and c.min() >= 100_000 and c.max() <= 2_000_000
     assert round(c.sum() / 1e6, 1) == 37.7
+
+
+def test_oracle_extrapolation_scales_gridding_by_visibilities_and_the_rest_by_planes():
+    """A sample plane of 4M of the job's 1e8 visibilities: gridding 2 s, the plane's image
+    10 s (8 s of FFT, screen and correction).  The job grids all 1e8 visibilities (25x the
+    sample) and transforms 32 planes."""
+    job = bench.oracle_job_seconds(2.0, 10.0, 4_000_000, 100_000_000, 32)
+    assert job == pytest.approx(25 * 2.0 + 32 * 8.0)
+    # a sample with every visibility of the job: gridding is billed once
+    assert bench.oracle_job_seconds(2.0, 10.0, 100, 100, 1) == pytest.approx(10.0)
