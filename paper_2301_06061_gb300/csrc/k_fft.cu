@@ -19,6 +19,10 @@
 //
 // Twiddles come from one table exp(+2 pi i m/N) rounded once from FP64; every
 // sub-length L divides N, so w_L^m = tw[m N/L].
+#include <cuda.h>  // CUtensorMap and the tensor-map encoder's types (the encoder is fetched at run time)
+
+#include <mutex>
+
 #include "fft_core.cuh"
 
 namespace wst {
@@ -742,6 +746,208 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
 }
 
 // ---------------------------------------------------------------------------------
+// Pass CB + K-P with TMA tile loads and a blocked Horner plane sum (LA = 64, 128).
+//
+// Tiles (LA rows x 16 columns of a plane, 128-byte row segments) are copied by the
+// tensor engine: one thread issues cp.async.bulk.tensor for a plane's tile into a ring of
+// three shared slots, each with an mbarrier that counts the copy's bytes; the ring runs
+// two planes ahead.  Every wait on a slot is bounded (wait_ns; on expiry the CTA records
+// WST_ERR_TIMEOUT, lets its copies in flight land and returns).  The transform is that of
+// k_cols_b16 (radix 16, in-place exchange in the slot, then LA/16), with two CTA barriers
+// per plane: one after the stage-0 reads (the slot of the previous plane is then free
+// and is refilled), one after the exchange.
+//
+// Plane sum (Eq. 2).  Within an image the screen of plane P at a pixel is
+// screen_P = screen_L s^(P - L) for any plane L, s = e^{2 pi i dw (n-1)} the pixel's step.
+// The planes are taken in anchor blocks of up to kAnchor; over a block with last plane L
+//   sum_P v_P screen_P = screen_L sum_P v_P conj(s)^(L - P),
+// evaluated by Horner's rule as the planes arrive, acc <- acc conj(s) + v_P (one complex
+// multiply-add per output and plane; |s| = 1).  At the block's last plane acc is
+// multiplied by the exact screen of that plane (float-float argument) and added, Kahan-
+// compensated, to the image's running sum; the next block starts from zero.  The
+// rounding of a block therefore stays within one block (as the recurrence of k_cols_b16
+// stays within kAnchor - 1 steps), and the blocks are summed with compensation.
+// ---------------------------------------------------------------------------------
+constexpr int kColsBRing = 3;
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_tile3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                                uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+template <int LA, bool FP64S, bool CROP>
+__global__ void __launch_bounds__(LA / 16 * kCB, LA == 128 ? 3 : 6)
+k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, Tw tw, int n, ScreenCtx sc,
+             float2 *__restrict__ image, float2 *__restrict__ comp, int flags, int n_img_arg, int crop_arg,
+             unsigned long long *__restrict__ err, unsigned long long wait_ns) {
+  const int n_img = CROP ? n_img_arg : n, crop = CROP ? crop_arg : 0;  // as in k_cols_b_acc
+  constexpr int EPT = 16, TPL = LA / EPT, THREADS = TPL * kCB, R1 = LA / 16;
+  static_assert(num_stages(LA, EPT) == 2 && stage_radix(LA, EPT, 1) == R1, "two stages");
+  constexpr uint32_t kTileBytes = LA * kCB * sizeof(float2);
+  static_assert(EPT * THREADS <= LA * kCB, "anchor screens fit a slot");
+  __shared__ __align__(128) float2 ring[kColsBRing][LA * kCB];
+  __shared__ float2 s_cstep[EPT][THREADS];  // conj of each output's per-plane screen step
+  constexpr int NTW = total_tw_count<LA, EPT>();
+  __shared__ float2 s_tw1[NTW][TPL];
+  __shared__ __align__(8) unsigned long long s_mbar[kColsBRing];
+  const int B = n / LA;
+  const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
+  const int c = blockIdx.y;
+  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
+  const int kp = col0 + col;
+  const bool kahan = flags & ACC_KAHAN;
+  const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&s_mbar[0]);
+  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(&ring[0][0]);
+  if (threadIdx.x < TPL) {
+    float2 twr[NTW];
+    all_twiddles<LA, EPT, TPL, 1>(twr, threadIdx.x, tw, B);
+#pragma unroll
+    for (int i = 0; i < NTW; ++i) s_tw1[i][threadIdx.x] = twr[i];
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kColsBRing; ++i) mbar_init(mbar0 + 8u * i, 1u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const int nplanes = p1 - p0;
+  int issued = 0;  // thread 0: planes (indices within the call) whose tile copy is issued
+  auto issue = [&](int q) {
+    const int slot = q % kColsBRing;
+    tma_load_tile3d(ring0 + (uint32_t)slot * kTileBytes, &tmap, 2 * col0, LA * c, q, mbar0 + 8u * slot, kTileBytes);
+  };
+  if (threadIdx.x == 0)
+    for (; issued < kColsBRing && issued < nplanes; ++issued) issue(issued);
+  // output e = b R1 + r of this thread is line element jt + b TPL + 16 r, image row c + B (that)
+  auto out_row = [&](int e) { return c + B * (jt + (e / R1) * TPL + 16 * (e % R1)); };
+  int P = p0;
+  bool failed = false;
+  while (P < p1 && !failed) {
+    const int img = P / n_w;
+    const int pstart = P;
+    const int pend = min(p1, (img + 1) * n_w);
+    // the per-plane step of each output for this image (exact), conjugated
+    {
+      const float2 dwI = FP64S ? make_float2(0.0f, 0.0f) : sc.dwff[img];
+#pragma unroll 1
+      for (int e = 0; e < EPT; ++e) {
+        const int kq = out_row(e);
+        float2 a, st;
+        if constexpr (FP64S) {
+          screen_anchor<true, true>(sc, kp, kq, P, img, 1.0f, a, st);
+        } else {
+          bool valid;
+          const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+          st = valid ? cis_cycles_ff(ff_mul({dwI.x, dwI.y}, t)) : make_float2(0.0f, 0.0f);
+        }
+        s_cstep[e][threadIdx.x] = make_float2(st.x, -st.y);
+      }
+    }
+    float2 S[EPT], Cc[EPT], acc[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) S[e] = Cc[e] = acc[e] = make_float2(0.0f, 0.0f);
+    for (; P < pend; ++P) {
+      const int q = P - p0;
+      const int slot = q % kColsBRing;
+      const bool ok = mbar_wait_bounded(mbar0 + 8u * slot, (uint32_t)(q / kColsBRing) & 1u, wait_ns);
+      float2 *tile = ring[slot];
+      float2 v[EPT];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = tile[(jt + r * TPL) * kCB + col];
+      dft<16, 1>(v);
+      if (__syncthreads_or(!ok)) {  // every stage-0 read of this slot and all of plane q - 1 done
+        failed = true;
+        break;
+      }
+      if (threadIdx.x == 0 && q >= 1 && issued < nplanes) {  // the slot of plane q - 1 is free
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(issued);
+        ++issued;
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) tile[(16 * jt + r) * kCB + col] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < EPT / R1; ++b)
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[b * R1 + r] = tile[(jt + b * TPL + 16 * r) * kCB + col];
+#pragma unroll
+      for (int b = 0; b < EPT / R1; ++b) {
+#pragma unroll
+        for (int r = 1; r < R1; ++r) v[b * R1 + r] = cmul(v[b * R1 + r], s_tw1[b * (R1 - 1) + r - 1][jt]);
+        dft<R1, 1>(&v[b * R1]);
+      }
+      // Horner: acc <- acc conj(s) + v
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float2 cs = s_cstep[e][threadIdx.x];
+        acc[e] = make_float2(fmaf(acc[e].x, cs.x, fmaf(-acc[e].y, cs.y, v[e].x)),
+                             fmaf(acc[e].x, cs.y, fmaf(acc[e].y, cs.x, v[e].y)));
+      }
+      if ((P - pstart) % kAnchor == kAnchor - 1 || P == pend - 1) {
+        // end of an anchor block: the exact screen of plane P (sign included) for each
+        // output, through the slot of this plane once every thread is done with it
+        __syncthreads();
+        float2 *s_anchor = tile;
+        const float2 wP = FP64S ? make_float2(0.0f, 0.0f) : sc.wc[P];
+#pragma unroll 1
+        for (int e = 0; e < EPT; ++e) {
+          const int kq = out_row(e);
+          const float sg = ((kq + kp) & 1) ? -1.0f : 1.0f;
+          float2 a, st;
+          if constexpr (FP64S) {
+            screen_anchor<true, false>(sc, kp, kq, P, img, sg, a, st);
+          } else {
+            bool valid;
+            const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+            a = valid ? cis_cycles_ff(ff_mul({wP.x, wP.y}, t)) : make_float2(0.0f, 0.0f);
+            a.x *= sg;
+            a.y *= sg;
+          }
+          s_anchor[e * THREADS + threadIdx.x] = a;
+        }
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const float2 y = cmul(acc[e], s_anchor[e * THREADS + threadIdx.x]);
+          if (kahan) kahan_add(S[e], Cc[e], y);
+          else S[e] = cadd(S[e], y);
+          acc[e] = make_float2(0.0f, 0.0f);
+        }
+      }
+    }
+    if (failed) break;
+    const bool first_any = img * n_w >= p0;
+    const bool last_any = (img + 1) * n_w <= p1;
+    float2 *im = image + (size_t)img * n_img * n_img;
+    float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int kq = out_row(e);
+      if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
+      const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
+      flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), S[e], Cc[e], first_any, last_any, flags, f);
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, (unsigned long long)WST_ERR_TIMEOUT);
+      // every copy issued must land before the CTA exits: bounded, with the full limit
+      for (int q = P - p0; q < issued; ++q)
+        mbar_wait_bounded(mbar0 + 8u * (q % kColsBRing), (uint32_t)(q / kColsBRing) & 1u, kWaitLimitNs);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // pass CB^H (adjoint): image tile -> planes; sign, correction and conjugate screen fused
 // ---------------------------------------------------------------------------------
 template <int LA, bool FP64S>
@@ -940,14 +1146,54 @@ static ScreenCtx screen_ctx(wst_plan_s *p) {
 
 static bool fp64_screen(const wst_plan_s *p) { return (p->cfg.flags & WST_FLAG_FP64_SCREEN) != 0; }
 
+// cuTensorMapEncodeTiled, fetched from the driver at run time (no link against libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of nplanes complex64 n x n planes seen as FP32 [nplanes][n][2n], with a box of
+// one tile: kCB complex columns (128 bytes) x `rows` rows x 1 plane.  False if the encoder
+// is unavailable or the buffer is not 16-byte aligned (the copies need both).
+static bool plane_tile_map(CUtensorMap *m, const float2 *planes, int n, int nplanes, int rows) {
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)planes & 15u) || nplanes < 1) return false;
+  const cuuint64_t dims[3] = {2ull * (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nplanes};
+  const cuuint64_t strides[2] = {8ull * (cuuint64_t)n, 8ull * (cuuint64_t)n * (cuuint64_t)n};
+  const cuuint32_t box[3] = {2u * kCB, (cuuint32_t)rows, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(planes), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int LA, bool FP64S, bool CROP>
 static void launch_cols_b_variant(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                   float2 *comp, int flags) {
   dim3 grd(p->n_img / kCB, p->n / LA);  // the image's column bands of the grid, every row block
-  if constexpr (LA == 64 || LA == 128)
-    k_cols_b16<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
-        planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
-  else
+  if constexpr (LA == 64 || LA == 128) {
+    CUtensorMap map;
+    if (plane_tile_map(&map, planes, p->n, p1 - p0, LA))
+      k_cols_b_tma<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
+          map, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop,
+          p->W_.counters + CNT_ERROR, p->wait_ns);
+    else
+      k_cols_b16<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
+          planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
+  } else
     k_cols_b_acc<LA, FP64S, CROP><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(
         planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
 }
