@@ -834,10 +834,13 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
     const int img = P / n_w;
     const int pstart = P;
     const int pend = min(p1, (img + 1) * n_w);
-    // the per-plane step of each output for this image (exact), conjugated
+    // the per-plane step of each output for this image (exact), conjugated.  The screen
+    // evaluations are long dependent chains (n - 1, float-float product, sincospi): four
+    // outputs at a time give the scheduler independent work without keeping all sixteen
+    // live; the results reach the unrolled plane loop through thread-private shared slots
     {
       const float2 dwI = FP64S ? make_float2(0.0f, 0.0f) : sc.dwff[img];
-#pragma unroll 1
+#pragma unroll 4
       for (int e = 0; e < EPT; ++e) {
         const int kq = out_row(e);
         float2 a, st;
@@ -898,7 +901,7 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
         __syncthreads();
         float2 *s_anchor = tile;
         const float2 wP = FP64S ? make_float2(0.0f, 0.0f) : sc.wc[P];
-#pragma unroll 1
+#pragma unroll 4
         for (int e = 0; e < EPT; ++e) {
           const int kq = out_row(e);
           const float sg = ((kq + kp) & 1) ? -1.0f : 1.0f;
