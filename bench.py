@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison of the transform stage")
+    ap.add_argument("--shard", choices=["replicas", "planes"], default="replicas",
+                    help="replicas: every rank images its own copy of the workload (weak scaling); planes: the "
+                         "ranks split one job's w-planes and sum the partial images with one all-reduce "
+                         "(strong scaling)")
     ap.add_argument("--dft-pixels", type=int, default=64)
     ap.add_argument("--n-w", type=int, default=0, help="override the number of w-planes (profiling cases)")
     ap.add_argument("--vis-frac", type=float, default=1.0, help="keep this fraction of the visibilities")
@@ -66,9 +70,11 @@ def parse():
                     help="2: grid of 2N cells, the central N x N kept (images up to 8192^2)")
     ap.add_argument("--wfold", action="store_true",
                     help="mirror w < 0 visibilities (WST_FLAG_WFOLD): half the w range; the real part is the image")
-    ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8"], default="gauss",
-                    help="gauss: W=7 Gaussian (the paper's); gauss8 / learned: W=8 Gaussian or the trained "
-                         "table (paper_2301_06061_gb300/data/learned_kernel_w8.npz)")
+    ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8", "es8", "kb8"], default="gauss",
+                    help="gauss: W=7 Gaussian (the paper's); W=8 kernels: gauss8 Gaussian (sigma 0.925), es8 "
+                         "exponential of semicircle (beta 2.3 W), kb8 Kaiser-Bessel table (beta of Beatty et "
+                         "al. for the grid's oversampling), learned the trained table "
+                         "(paper_2301_06061_gb300/data/learned_kernel_w8.npz)")
     return ap.parse_args()
 
 
@@ -129,10 +135,17 @@ def random_values(work, rank: int):
 # ------------------------------------------------------------------------------------------
 
 def kernel_function(kernel: str, support: int, sigma: float, table):
+    """(G, quadrature panels) of a kernel: a tabulated one (learned, kb8) interpolated
+    linearly as the library does, es8's exponential of semicircle (sigma holds beta), or
+    the Gaussian."""
     half = 0.5 * support
-    if kernel == "learned":
+    if table is not None:
         nodes = np.linspace(-half, half, table.size)
         return lambda t: np.interp(t, nodes, table.astype(np.float64)), table.size - 1
+    if kernel == "es8":
+        return (lambda t: np.where(np.abs(t) <= half,
+                                   np.exp(sigma * (np.sqrt(np.clip(1.0 - (t / half) ** 2, 0.0, None)) - 1.0)), 0.0),
+                support * 64)
     return lambda t: np.exp(-t * t / (2.0 * sigma * sigma)), support * 64
 
 
@@ -164,7 +177,7 @@ def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np
 
 
 def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev, n_pix: int, kernel: str,
-                   support: int, sigma: float, table, wfold: bool = False, oversample: int = 1):
+                   support: int, sigma: float, table, wfold: bool = False, oversample: int = 1, plan=None):
     """The image against the direct transform (GPU, float-float phases) at the brightest
     sources' pixels and at seeded random pixels, with the per-pixel bound
     B = sum|V| (min(2, 2 pi dmax |n - 1|) + e_a + e_b + e_a e_b) + 1e-5 peak, dmax the
@@ -184,7 +197,16 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     d_pa = torch.from_numpy(pa.astype(np.int32)).to(dev)
     d_pb = torch.from_numpy(pb.astype(np.int32)).to(dev)
     dft = torch.empty(pa.size, dtype=torch.complex64, device=dev)
-    wst.wst_dft(d_u, d_v, d_w, d_vis, n, fov, d_pa, d_pb, dft)
+    # the direct transform of the visibilities the image holds: those the sort dropped
+    # (footprint off the grid) or found non-finite get weight 0
+    kept = None
+    if plan is not None:
+        k = torch.empty(d_u.numel(), dtype=torch.int32, device=dev)
+        i0, j0 = torch.empty_like(k), torch.empty_like(k)
+        wst.wst_vis_cells(plan.handle, k, i0, j0)
+        kept = (k >= 0).float()
+        del k, i0, j0
+    wst.wst_dft(d_u, d_v, d_w, d_vis, n, fov, d_pa, d_pb, dft, weight=kept)
     got = img[0][d_pb.long(), d_pa.long()]
     if wfold:
         err = (got.real - dft.real).abs().double().cpu().numpy()
@@ -193,7 +215,7 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
         err = (got - dft).abs().double().cpu().numpy()
         dft_abs = dft.abs().double().cpu().numpy()
     peak = dft_abs.max()
-    sum_abs = float(d_vis.abs().double().sum().item())
+    sum_abs = float((d_vis.abs().double() * (1.0 if kept is None else kept.double())).sum().item())
     # largest |w - w_k| over the data, w_k the centre of the plane the visibility lands on
     lo, hi = float(plan_stats["w_min"]), float(plan_stats["w_max"])
     w64 = d_w.double().abs() if wfold else d_w.double()
@@ -209,7 +231,9 @@ def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev,
     bound = sum_abs * rel + 1e-5 * peak
     central = (np.abs(pa - n // 2) < n // 8) & (np.abs(pb - n // 2) < n // 8)
     inner = (np.abs(pa - n // 2) < 3 * n // 8) & (np.abs(pb - n // 2) < 3 * n // 8)  # central 3/4
-    return {"reference": "wst_dft (GPU direct transform of Eq. 2 with float-float phases)",
+    return {"reference": "wst_dft (GPU direct transform of Eq. 2 with float-float phases) of the gridded "
+                         "visibilities (dropped ones excluded)",
+            "excluded_visibilities": None if kept is None else int(kept.numel() - kept.sum().item()),
             "sky": f"{sky.flux.size} point sources, visibilities by Eq. 1 (wst_predict_points)",
             "pixels": int(pa.size), "source_pixels": int(sa.size),
             "max_err_rel_peak": float(err.max() / peak),
@@ -512,10 +536,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         kcfg = dict(support=work.support, kparam=wst.DEFAULT_SIGMA[work.support])
     elif args.kernel == "gauss8":
         kcfg = dict(support=8, kparam=wst.DEFAULT_SIGMA[8])
+    elif args.kernel == "es8":
+        kcfg = dict(support=8, kernel=wst.WST_KERNEL_ES, kparam=2.3 * 8)
     else:
-        from paper_2301_06061_gb300 import learned
+        if args.kernel == "kb8":
+            from paper_2301_06061_gb300 import kernels
 
-        tab_np = learned.load_table(os.path.join(ROOT, "paper_2301_06061_gb300", "data", "learned_kernel_w8.npz"))
+            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, float(max(1, args.oversample))))
+        else:
+            from paper_2301_06061_gb300 import learned
+
+            tab_np = learned.load_table(os.path.join(ROOT, "paper_2301_06061_gb300", "data", "learned_kernel_w8.npz"))
         table = torch.from_numpy(tab_np).to(dev)
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
     cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
@@ -670,7 +701,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         sigma = kcfg.get("kparam", 0.0)
         acc = accuracy_block(torch, wst, work, st, d_u, d_v, d_w, d_vis, img, dev, args.dft_pixels,
                              args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold,
-                             max(1, args.oversample))
+                             max(1, args.oversample), plan=plan)
         if not args.snap_w and not args.wfold:
             # the same visibilities with every w moved to its plane's centre: the error
             # against the direct transform is then the (u, v) kernel's alone
@@ -687,7 +718,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             plan.image(out=img)
             snapped = accuracy_block(torch, wst, work, plan.stats(), d_u, d_v, d_ws, d_vis, img, dev,
                                      args.dft_pixels, args.kernel, cfg.support, sigma,
-                                     None if table is None else tab_np, False, max(1, args.oversample))
+                                     None if table is None else tab_np, False, max(1, args.oversample), plan=plan)
             acc["w_snapped"] = {k2: snapped[k2] for k2 in (
                 "max_err_rel_peak", "central_max_err_rel_peak", "inner3q_max_err_rel_peak",
                 "inner3q_rms_err_rel_peak", "max_err_over_bound", "bound_rel_peak", "kernel_error_max")}
@@ -722,6 +753,108 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                               "transforms the rows"},
             "gpu_launches": int(st["n_launches"]) * args.steps, "accuracy": acc,
         }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_sharded(args, rank: int, world: int, local_rank: int):
+    """One job split over the ranks by w-plane (paper_2301_06061_gb300/shard.py): rank r
+    binds the visibilities that the library places in its range of planes, images that
+    range (wst_image_range), and the partial images are summed by one all-reduce.  The
+    timed step is set_vis + image_range + the all-reduce; value = the job's visibilities
+    over the slowest rank's time."""
+    import torch
+
+    from paper_2301_06061_gb300 import build, shard, wst
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    work = make_workload(args.workload, 0, args.n_w, args.vis_frac)  # the same job on every rank
+    batch = 1 if work.batch_offsets is None else len(work.batch_offsets) - 1
+    if batch != 1:
+        raise SystemExit("--shard planes images single-image workloads")
+    kw = dict(support=work.support, kparam=wst.DEFAULT_SIGMA[work.support])
+    d_u, d_v, d_w = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (work.u, work.v, work.w))
+    d_vis = torch.empty(work.n_vis, dtype=torch.complex64, device=dev)
+    sky_t = [torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
+             for a in (work.sky.l, work.sky.m, work.sky.flux)]
+    wst.wst_predict_points(d_u, d_v, d_w, *sky_t, d_vis)
+    # set-up: the plane of every visibility as the sort assigns it, and the job's w range
+    full = wst.Plan(wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
+                               flags=wst.WST_FLAG_KAHAN, planes_per_chunk=1, **kw), device=dev)
+    full.set_vis(d_u, d_v, d_w, d_vis)
+    k = torch.empty(work.n_vis, dtype=torch.int32, device=dev)
+    i0, j0 = torch.empty_like(k), torch.empty_like(k)
+    wst.wst_vis_cells(full.handle, k, i0, j0)
+    st_full = full.stats()
+    full.close()
+    del i0, j0
+    lo, hi = float(st_full["w_min"]), float(st_full["w_max"])
+    b, e = shard.plane_ranges(work.n_w, world)[rank]
+    own = shard.owned(k, b, e)
+    r_u, r_v, r_w, r_vis = d_u[own].contiguous(), d_v[own].contiguous(), d_w[own].contiguous(), d_vis[own].contiguous()
+    del k, own
+    plan = wst.Plan(wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=lo, w_max=hi,
+                               flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING, planes_per_chunk=args.chunk, **kw),
+                    device=dev)
+    img = torch.empty((1, work.n, work.n), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.set_vis(r_u, r_v, r_w, r_vis)
+        plan.image_range(b, e, out=img)
+        shard.reduce_images(img, dist)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    st = plan.stats()
+    # the reduced image against a single-plan image of the whole job (outside the timed region)
+    check = None
+    if rank == 0:
+        whole = wst.Plan(wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=lo, w_max=hi,
+                                    flags=wst.WST_FLAG_KAHAN, planes_per_chunk=min(8, work.n_w), **kw), device=dev)
+        whole.set_vis(d_u, d_v, d_w, d_vis)
+        ref = whole.image()
+        check = float((img - ref).abs().max() / ref.abs().max())
+        whole.close()
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(work.n_vis / (ms_step * 1e-3) / 1e6, 2), "unit": "Mvis/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
+                       "n_vis": work.n_vis, "parallelism": f"w-plane shards x{world}, one all-reduce of the image",
+                       "planes_of_rank0": [b, e], "vis_of_rank0": int(r_u.numel()),
+                       "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)"},
+            "stage_ms_per_step_rank0": {k2: round(st[k2] / args.steps, 4) for k2 in
+                                        ("ms_sort", "ms_grid", "ms_cols_a", "ms_cols_b")},
+            "reduced_vs_single_plan_max_diff_rel_peak": check, "clocks": clocks,
+            "gpu_launches": int(st["n_launches"]) * args.steps, "e2e": None,
+            "e2e_note": "the sharded mode times device-resident inputs; the replicas mode reports e2e"}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
@@ -771,6 +904,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.shard == "planes":
+        run_sharded(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

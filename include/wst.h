@@ -241,20 +241,38 @@ wst_status wst_correct(wst_plan plan, void *image_inout);
 wst_status wst_image(wst_plan plan, void *image_out, uint32_t flags);
 
 /*
+ * wst_image restricted to the global planes [plane_begin, plane_end) (plane index
+ * image * N_w + k): image_out[i] = the grid-corrected (unless WST_NO_CORRECTION) sum of
+ * Eq. 2 over the planes of image i in the range, zero for images with no plane in it.
+ * The paper divides the mesh among MPI tasks and reduces their partial results into
+ * the image (section 3.1, the slab decomposition, and section 3.2, the reduce of each
+ * slab); here each process (one GPU) images a range of w-planes and the caller sums the
+ * partial images (one all-reduce): Eq. 2 is a sum over planes and the grid correction
+ * is linear, so the partial images of ranges that partition [0, batch * N_w) add up to
+ * wst_image.  Layout, memory and chunking as wst_image.  Errors: INVALID_ARG (range).
+ */
+wst_status wst_image_range(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *image_out,
+                           uint32_t flags);
+
+/*
  * Adjoint of wst_image (degridding; the paper lists it as future work in its
  * conclusions): dvis_j = w_j sum_taps G G g_k[q,p], g_k the centred 2D transform
  * with the negative exponent of conj(screen_k) * C_a C_b * dimage.
- * WST_ERR_UNSUPPORTED with WST_FLAG_WFOLD or an oversampled grid.
- * dimage: complex64 [batch x N x N]; dvis_out: complex64 [n_vis] in the caller's
- * order (0 for dropped and non-finite visibilities).
+ * WST_ERR_UNSUPPORTED with WST_FLAG_WFOLD.  With an oversampled grid (oversample = 2)
+ * the image enters the grid zero-padded around its central N x N, the adjoint of the
+ * forward crop.  dimage: complex64 [batch x N x N]; dvis_out: complex64 [n_vis] in the
+ * caller's order (0 for dropped and non-finite visibilities).
  */
 wst_status wst_degrid(wst_plan plan, const void *dimage, void *dvis_out, uint32_t flags);
 
 /*
  * WST_KERNEL_TABLE only: gradient of Re<dimage, U> with respect to the kernel
  * samples, U the image without grid correction (WST_NO_CORRECTION must be set:
- * the correction's dependence on the table is left to the caller).
- * dtable_out: FP32 [ktable_len], overwritten.
+ * the correction's dependence on the table is left to the caller).  The kernel G of
+ * Eq. 3 is the imager's free choice (section 2 uses a Gaussian of 7 cells; the
+ * conclusions name better convolution kernels as future work): this gradient lets a
+ * caller fit the table.  On an oversampled grid dimage enters zero-padded, as in
+ * wst_degrid.  dtable_out: FP32 [ktable_len], overwritten.
  */
 wst_status wst_kernel_grad(wst_plan plan, const void *dimage, float *dtable_out, uint32_t flags);
 

@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     OracleConfig,
     build,
     degrid,
+    degrid_oversampled,
     dft_pixels,
     expand_rows,
     fft1d,
@@ -25,6 +26,7 @@ from .oracle import (  # noqa: F401
     kernel_eval,
     kernel_ft,
     kernel_grad,
+    kernel_grad_oversampled,
     locate,
     n_minus_one,
     num_threads,

@@ -20,6 +20,9 @@ Every function follows a passage of arXiv:2301.06061:
                        (not in the paper; applied to the inputs of the functions above)
 * ``image_oversampled`` -- the oversampled-grid variant (not in the paper): ``image``
                        on a grid of 2N cells, cropped to the central N x N
+* ``degrid_oversampled``, ``kernel_grad_oversampled`` -- its adjoint and kernel gradient:
+                       the image zero-padded to the grid (the adjoint of the crop), then
+                       ``degrid`` / ``kernel_grad`` on the grid
 * ``expand_rows``   -- per-visibility (u, v, w) in wavelengths from per-row baseline
                        coordinates in metres and per-channel nu / c (the layout of
                        the LOFAR datasets of section 4; input expansion only)
@@ -32,6 +35,8 @@ dot-product identity for the adjoint; finite differences for the kernel
 gradient; exact integer placement rules for ``locate``; for ``fold_w``, the
 invariance of the real part of the direct transform; for ``image_oversampled``, the
 direct transform within the aliasing bound of the half-band frequencies; for
+``degrid_oversampled``, the dot-product identity with ``image_oversampled``; for
+``kernel_grad_oversampled``, central differences of ``image_oversampled``; for
 ``expand_rows``, exactly representable products, the (row, channel) order with a
 partial last row, and a product whose one rounding differs from rounding its factors
 first.
@@ -297,6 +302,33 @@ def image_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, weight=N
     full = image(big, u, v, w, vis, weight, correct)
     c = (n * oversample - n) // 2
     return full[c:c + n, c:c + n].copy()
+
+
+def _big(cfg: OracleConfig, oversample: int) -> OracleConfig:
+    return OracleConfig(cfg.n * oversample, cfg.fov * oversample, cfg.n_w, cfg.w_min, cfg.w_max, cfg.support,
+                        cfg.kernel, cfg.kparam, cfg.ktable)
+
+
+def _zero_pad(dimage, n: int, oversample: int) -> np.ndarray:
+    """The N x N image in the centre of a zero (oversample N)^2 grid image: the adjoint of
+    the centre crop of ``image_oversampled``."""
+    big = np.zeros((n * oversample, n * oversample), np.complex128)
+    c = (n * oversample - n) // 2
+    big[c:c + n, c:c + n] = np.asarray(dimage, np.complex128).reshape(n, n)
+    return big
+
+
+def degrid_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, dimage, weight=None,
+                       correct: bool = True) -> np.ndarray:
+    """Adjoint of ``image_oversampled``: the image is zero-padded to the (oversample N)^2
+    grid (the adjoint of the crop) and degridded by ``degrid`` on that grid."""
+    return degrid(_big(cfg, oversample), u, v, w, vis, _zero_pad(dimage, cfg.n, oversample), weight, correct)
+
+
+def kernel_grad_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, dimage, weight=None) -> np.ndarray:
+    """Gradient of Re<dimage, U> w.r.t. the kernel table, U the uncorrected
+    ``image_oversampled``: ``kernel_grad`` on the grid with the zero-padded dimage."""
+    return kernel_grad(_big(cfg, oversample), u, v, w, vis, _zero_pad(dimage, cfg.n, oversample), weight)
 
 
 def image_pixels(cfg: OracleConfig, u, v, w, vis, pa, pb, weight=None,

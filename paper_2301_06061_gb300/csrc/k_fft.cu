@@ -444,8 +444,10 @@ __device__ __forceinline__ void screen_from_t(float2 t2, float2 w, float2 dw, fl
   scr.y *= scale;
 }
 
-// epilogue modes
-enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16 };
+// epilogue modes.  ACC_RANGE_START / ACC_RANGE_END: the call's first (last) plane starts
+// (ends) the requested plane range, so every image the chunk touches starts (finishes)
+// its sum here even if its first (last) plane lies outside the range.
+enum { ACC_CORRECT = 4, ACC_KAHAN = 8, ACC_STAGED = 16, ACC_RANGE_START = 32, ACC_RANGE_END = 64 };
 
 // ---------------------------------------------------------------------------------
 // pass CB (forward) + K-P: length-LA DFT over rows A*c + a, then the centring sign and
@@ -599,8 +601,8 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
     }
     // flush this image's tile: its sum starts in this chunk if its first plane is at
     // or after p0, and is complete if its last plane is before p1
-    const bool first_any = img * n_w >= p0;
-    const bool last_any = (img + 1) * n_w <= p1;
+    const bool first_any = img * n_w >= p0 || (flags & ACC_RANGE_START);
+    const bool last_any = (img + 1) * n_w <= p1 || (flags & ACC_RANGE_END);
     float2 *im = image + (size_t)img * n_img * n_img;
     float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
@@ -728,8 +730,8 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       }
       __syncthreads();  // staging buffer reused by the next planes
     }
-    const bool first_any = img * n_w >= p0;
-    const bool last_any = (img + 1) * n_w <= p1;
+    const bool first_any = img * n_w >= p0 || (flags & ACC_RANGE_START);
+    const bool last_any = (img + 1) * n_w <= p1 || (flags & ACC_RANGE_END);
     float2 *im = image + (size_t)img * n_img * n_img;
     float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
@@ -927,8 +929,8 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
       }
     }
     if (failed) break;
-    const bool first_any = img * n_w >= p0;
-    const bool last_any = (img + 1) * n_w <= p1;
+    const bool first_any = img * n_w >= p0 || (flags & ACC_RANGE_START);
+    const bool last_any = (img + 1) * n_w <= p1 || (flags & ACC_RANGE_END);
     float2 *im = image + (size_t)img * n_img * n_img;
     float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
@@ -953,10 +955,12 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
 // ---------------------------------------------------------------------------------
 // pass CB^H (adjoint): image tile -> planes; sign, correction and conjugate screen fused
 // ---------------------------------------------------------------------------------
+// An image smaller than the grid (oversampled grid: the image is the central n_img x
+// n_img from grid index crop) enters zero-padded: the adjoint of the forward crop.
 template <int LA, bool FP64S>
 __global__ void __launch_bounds__(ColCfg<LA>::THREADS)
 k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, Tw tw,
-          int n, ScreenCtx sc, int correct, float2 *__restrict__ planes) {
+          int n, ScreenCtx sc, int correct, float2 *__restrict__ planes, int n_img, int crop) {
   using C = ColCfg<LA>;
   constexpr int EPT = C::EPT, TPL = C::TPL;
   constexpr int NST = num_stages(LA, EPT);
@@ -974,13 +978,16 @@ k_cols_bh(const float2 *__restrict__ dimage, int p0, int p1, int n_w, Tw tw,
   for (int P = p0; P < p1; ++P) {
     const int img = P / n_w;
     if (img != img_loaded) {
-      const float2 *im = dimage + (size_t)img * n * n;
+      const float2 *im = dimage + (size_t)img * n_img * n_img;
+      const bool col_in = kp >= crop && kp < crop + n_img;
 #pragma unroll
       for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
-          const int d = in_index<LA, EPT, TPL, 0>(jt, b, r);
-          dv[b * R0 + r] = im[(size_t)(c + B * d) * n + kp];
+          const int kq = c + B * in_index<LA, EPT, TPL, 0>(jt, b, r);
+          dv[b * R0 + r] = (col_in && kq >= crop && kq < crop + n_img)
+                               ? im[(size_t)(kq - crop) * n_img + (kp - crop)]
+                               : make_float2(0.0f, 0.0f);
         }
       img_loaded = img;
       pstart = P;
@@ -1213,10 +1220,13 @@ static cudaError_t launch_cols_b(wst_plan_s *p, const float2 *planes, int p0, in
 }
 
 cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
-                                  float2 *comp, bool kahan, bool correct, bool staged_add) {
+                                  float2 *comp, bool kahan, bool correct, bool staged_add, bool range_start,
+                                  bool range_end) {
   if (p1 <= p0) return cudaSuccess;
   p->launches += 1;
   int flags = 0;
+  if (range_start) flags |= ACC_RANGE_START;
+  if (range_end) flags |= ACC_RANGE_END;
   if (correct) flags |= ACC_CORRECT;
   if (kahan) flags |= ACC_KAHAN;
   if (staged_add) flags |= ACC_STAGED;
@@ -1235,11 +1245,11 @@ static cudaError_t launch_cols_bh(wst_plan_s *p, const float2 *dimage, int p0, i
                                   bool correct) {
   dim3 grd(p->n / kCB, p->n / LA);
   if (fp64_screen(p))
-    k_cols_bh<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                     screen_ctx(p), correct ? 1 : 0, planes);
+    k_cols_bh<LA, true><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(
+        dimage, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), correct ? 1 : 0, planes, p->n_img, p->crop);
   else
-    k_cols_bh<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(dimage, p0, p1, p->n_w, tw_of(p), p->n,
-                                                                      screen_ctx(p), correct ? 1 : 0, planes);
+    k_cols_bh<LA, false><<<grd, ColCfg<LA>::THREADS, 0, p->stream>>>(
+        dimage, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), correct ? 1 : 0, planes, p->n_img, p->crop);
   return cudaGetLastError();
 }
 

@@ -268,7 +268,6 @@ wst_status wst_plan_set_kernel_table(wst_plan p, const float *table_dev) {
   if (!p) return WST_ERR_INVALID_ARG;
   if (p->cfg.kernel != WST_KERNEL_TABLE) return fail(p, WST_ERR_STATE, "plan kernel is not a table");
   if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no kernel gradient with WST_FLAG_WFOLD");
-  if (p->crop) return fail(p, WST_ERR_UNSUPPORTED, "no kernel gradient with an oversampled grid");
   if (!table_dev) return fail(p, WST_ERR_INVALID_ARG, "table pointer is NULL");
   WST_CUDA(p, cudaMemcpyAsync(p->ktable, table_dev, sizeof(float) * p->cfg.ktable_len,
                               cudaMemcpyDeviceToDevice, p->stream), "table copy");
@@ -437,20 +436,29 @@ wst_status wst_correct(wst_plan p, void *image) {
   return WST_OK;
 }
 
-wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
+// The plane sum over global planes [b, e) of every image they touch, chunk by chunk;
+// images that no plane of the range belongs to are set to zero.
+static wst_status image_range(wst_plan_s *p, int b, int e, void *image_out, uint32_t flags) {
   wst_status st = check_ready(p);
   if (st) return st;
   if (!image_out) return fail(p, WST_ERR_INVALID_ARG, "NULL image");
   if (flags & ~WST_NO_CORRECTION) return fail(p, WST_ERR_INVALID_ARG, "unknown flags");
+  if (b < 0 || e > p->n_planes || b > e) return fail(p, WST_ERR_INVALID_ARG, "plane range");
   const bool correct = !(flags & WST_NO_CORRECTION);
   const bool kahan = (p->cfg.flags & WST_FLAG_KAHAN) != 0;
   float2 *img = (float2 *)device_view(p, image_out);
   if (!img) return fail(p, WST_ERR_INVALID_ARG, "image must be device or page-locked host memory");
+  const size_t img_bytes = sizeof(float2) * (size_t)p->n_img * p->n_img;
+  // images outside the range hold no plane of it: zero
+  const int i0 = b < e ? b / p->n_w : p->batch, i1 = b < e ? (e - 1) / p->n_w + 1 : p->batch;
+  if (i0 > 0) WST_CUDA(p, cudaMemsetAsync(img, 0, img_bytes * i0, p->stream), "memset");
+  if (i1 < p->batch) WST_CUDA(p, cudaMemsetAsync(img + (size_t)i1 * p->n_img * p->n_img, 0,
+                                                 img_bytes * (p->batch - i1), p->stream), "memset");
   float2 *planes = p->W_.planes;
   p->n_chunks = 0;
   p->launches = 0;
-  for (int p0 = 0; p0 < p->n_planes; p0 += p->chunk) {
-    const int p1 = (p0 + p->chunk < p->n_planes) ? p0 + p->chunk : p->n_planes;
+  for (int p0 = b; p0 < e; p0 += p->chunk) {
+    const int p1 = (p0 + p->chunk < e) ? p0 + p->chunk : e;
     WST_CUDA(p, time_begin(p, p->ev_img, ST_GRID), "event");
     WST_CUDA(p, grid_rows(p, p0, p1, planes, true), "grid + rows");
     WST_CUDA(p, time_end(p, p->ev_img), "event");
@@ -458,12 +466,23 @@ wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
     WST_CUDA(p, fft_cols_a(p, planes, p1 - p0, +1, false, p->W_.occ), "cols A");
     WST_CUDA(p, time_end(p, p->ev_img), "event");
     WST_CUDA(p, time_begin(p, p->ev_img, ST_COLS_B), "event");
-    WST_CUDA(p, fft_cols_b_accumulate(p, planes, p0, p1, img, p->W_.comp, kahan, correct, false), "cols B");
+    WST_CUDA(p, fft_cols_b_accumulate(p, planes, p0, p1, img, p->W_.comp, kahan, correct, false, p0 == b, p1 == e),
+             "cols B");
     WST_CUDA(p, time_end(p, p->ev_img), "event");
     ++p->n_chunks;
   }
   p->launches_image = p->launches;
   return WST_OK;
+}
+
+wst_status wst_image(wst_plan p, void *image_out, uint32_t flags) {
+  if (!p) return WST_ERR_INVALID_ARG;
+  return image_range(p, 0, p->n_planes, image_out, flags);
+}
+
+wst_status wst_image_range(wst_plan p, int32_t plane_begin, int32_t plane_end, void *image_out, uint32_t flags) {
+  if (!p) return WST_ERR_INVALID_ARG;
+  return image_range(p, plane_begin, plane_end, image_out, flags);
 }
 
 wst_status wst_degrid(wst_plan p, const void *dimage, void *dvis, uint32_t flags) {
@@ -472,7 +491,6 @@ wst_status wst_degrid(wst_plan p, const void *dimage, void *dvis, uint32_t flags
   if (!dimage || (!dvis && p->n_vis > 0)) return fail(p, WST_ERR_INVALID_ARG, "NULL buffer");
   if (flags & ~WST_NO_CORRECTION) return fail(p, WST_ERR_INVALID_ARG, "unknown flags");
   if (p->cfg.flags & WST_FLAG_WFOLD) return fail(p, WST_ERR_UNSUPPORTED, "no adjoint with WST_FLAG_WFOLD");
-  if (p->crop) return fail(p, WST_ERR_UNSUPPORTED, "no adjoint with an oversampled grid");
   const bool correct = !(flags & WST_NO_CORRECTION);
   if (p->n_vis > 0) WST_CUDA(p, cudaMemsetAsync(dvis, 0, sizeof(float2) * p->n_vis, p->stream), "memset");
   float2 *planes = p->W_.planes;

@@ -307,10 +307,12 @@ cudaError_t fft_rows(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool p
 // occ (nullable): per (plane of the call, row) 0 if the row is known to be zero
 cudaError_t fft_cols_a(wst_plan_s *p, float2 *planes, int nplanes, int dir, bool twiddle_first,
                        const uint8_t *occ);
-// forward: accumulate planes [p0,p1) (stored at planes[0..]) into image (+comp)
+// forward: accumulate planes [p0,p1) (stored at planes[0..]) into image (+comp); range_start
+// (range_end): p0 (p1) is the start (end) of the requested plane range, so the images the
+// call touches start (finish) their sums in it
 cudaError_t fft_cols_b_accumulate(wst_plan_s *p, const float2 *planes, int p0, int p1,
                                   float2 *image, float2 *comp, bool kahan, bool correct,
-                                  bool staged_add);
+                                  bool staged_add, bool range_start = false, bool range_end = false);
 // adjoint: planes [p0,p1) from the image tile: sign * conj(screen) * corr * dimage, DFT(-1)
 cudaError_t fft_cols_bh_from_image(wst_plan_s *p, const float2 *dimage, int p0, int p1,
                                    float2 *planes, bool correct);

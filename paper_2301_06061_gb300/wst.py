@@ -29,7 +29,7 @@ WST_NO_CORRECTION = 0x1
 EXPORTED = [
     "wst_version", "wst_status_string", "wst_plan_create", "wst_plan_destroy", "wst_plan_set_stream",
     "wst_plan_set_wait_limit", "wst_plan_workspace_bytes", "wst_plan_set_workspace", "wst_plan_set_kernel_table",
-    "wst_plan_set_vis", "wst_plan_set_vis_rows", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_degrid",
+    "wst_plan_set_vis", "wst_plan_set_vis_rows", "wst_grid", "wst_fft_correct", "wst_correct", "wst_image", "wst_image_range", "wst_degrid",
     "wst_kernel_grad", "wst_vis_cells", "wst_get_stats", "wst_last_error", "wst_dft",
     "wst_predict_points", "wst_dft_noalloc",
 ]
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
             "wst_fft_correct": ([P, I32, I32, P, P], ctypes.c_int),
             "wst_correct": ([P, P], ctypes.c_int),
             "wst_image": ([P, P, U32], ctypes.c_int),
+            "wst_image_range": ([P, I32, I32, P, U32], ctypes.c_int),
             "wst_degrid": ([P, P, P, U32], ctypes.c_int),
             "wst_kernel_grad": ([P, P, P, U32], ctypes.c_int),
             "wst_vis_cells": ([P, P, P, P], ctypes.c_int),
@@ -254,6 +255,12 @@ def wst_image(plan, image_out: torch.Tensor, flags: int = 0) -> None:
     _check(load_library().wst_image(plan, _ptr(image_out, True), flags), "wst_image", plan)
 
 
+def wst_image_range(plan, plane_begin: int, plane_end: int, image_out: torch.Tensor, flags: int = 0) -> None:
+    assert image_out.dtype == torch.complex64
+    _check(load_library().wst_image_range(plan, int(plane_begin), int(plane_end), _ptr(image_out, True), flags),
+           "wst_image_range", plan)
+
+
 def wst_degrid(plan, dimage: torch.Tensor, dvis_out: torch.Tensor, flags: int = 0) -> None:
     assert dimage.dtype == torch.complex64 and dvis_out.dtype == torch.complex64
     _check(load_library().wst_degrid(plan, _ptr(dimage), _ptr(dvis_out), flags), "wst_degrid", plan)
@@ -388,6 +395,15 @@ class Plan:
             out = torch.empty((c.batch, c.n, c.n), dtype=torch.complex64, device=self.device)
         wst_plan_stream(self.handle)
         wst_image(self.handle, out, flags)
+        return out
+
+    def image_range(self, plane_begin: int, plane_end: int, out=None, flags: int = 0) -> torch.Tensor:
+        """The partial image of global planes [plane_begin, plane_end) (wst_image_range)."""
+        c = self.cfg
+        if out is None:
+            out = torch.empty((c.batch, c.n, c.n), dtype=torch.complex64, device=self.device)
+        wst_plan_stream(self.handle)
+        wst_image_range(self.handle, plane_begin, plane_end, out, flags)
         return out
 
     def degrid(self, dimage, out=None, flags: int = 0) -> torch.Tensor:

@@ -151,6 +151,7 @@ def test_every_entry_point_rejects_a_null_plan_or_bad_sizes_without_a_device(lib
         "wst_fft_correct": (None, 0, 1, None, None),
         "wst_correct": (None, None),
         "wst_image": (None, None, 0),
+        "wst_image_range": (None, 0, 1, None, 0),
         "wst_degrid": (None, None, None, 0),
         "wst_kernel_grad": (None, None, None, 0),
         "wst_vis_cells": (None, None, None, None),

@@ -240,3 +240,46 @@ def test_degrid_matches_fp64_central_differences_of_the_oracle_image(wst):
     plan.set_vis(dev(u), dev(v), dev(w), dev(vis), dev(wt))
     got = plan.degrid(dev(y.astype(np.complex64)[None])).cpu().numpy()[picks].astype(np.complex128)
     assert np.abs(got - fd).max() < TOL * np.abs(fd).max()
+
+
+@pytest.mark.parametrize("n,chunk,correct", [(256, 0, True), (256, 2, False), (4096, 0, True)])
+def test_degrid_on_the_oversampled_grid_matches_oracle(wst, n, chunk, correct):
+    """wst_degrid of a plan with oversample = 2 (grid 2N): the image enters zero-padded
+    into the grid (the adjoint of the forward crop), against oracle.degrid_oversampled."""
+    u, v, w, vis, wt, rng = case(n=n, seed=50 + n, n_vis=3000)
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0, planes_per_chunk=chunk, oversample=2)
+    plan = wst.Plan(cfg)
+    plan.set_vis(dev(u), dev(v), dev(w), dev(vis), dev(wt))
+    y = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    flags = 0 if correct else wst.WST_NO_CORRECTION
+    got = plan.degrid(dev(y[None]), flags=flags).cpu().numpy()
+    ref = oracle.degrid_oversampled(OracleConfig(n, 0.1, 3, -200.0, 200.0, 7), 2, u, v, w, vis, y, wt,
+                                    correct=correct)
+    assert rel_err(got, ref) < TOL
+    # and the GPU's own dot-product identity with its forward image
+    ax = plan.image(flags=flags)[0].cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(y.astype(np.complex128), ax)
+    rhs = np.vdot(got.astype(np.complex128), vis.astype(np.complex128))
+    assert abs(lhs - rhs) < (1e-5 if not correct else 1e-4) * abs(lhs)
+
+
+def test_table_kernel_and_its_gradient_on_the_oversampled_grid(wst):
+    n, W = 256, 8
+    L = W * 32 + 1
+    u, v, w, vis, wt, rng = case(n=n, n_vis=1500, seed=61)
+    xs = np.linspace(-W / 2, W / 2, L)
+    tab = (np.exp(-xs**2 / (2 * 0.925**2)) * (1 + 0.05 * np.sin(xs))).astype(np.float32)
+    cfg = wst.Config(n=n, fov=0.1, n_w=3, w_min=-200.0, w_max=200.0, support=W, kernel=wst.WST_KERNEL_TABLE,
+                     ktable_len=L, kparam=0.0, planes_per_chunk=2, oversample=2)
+    plan = wst.Plan(cfg)
+    plan.set_kernel_table(dev(tab))
+    plan.set_vis(dev(u), dev(v), dev(w), dev(vis), dev(wt))
+    ocfg = OracleConfig(n, 0.1, 3, -200.0, 200.0, W, "table", 0.0, tab.astype(np.float64))
+    img = plan.image(flags=wst.WST_NO_CORRECTION)[0].cpu().numpy()
+    assert rel_err(img, oracle.image_oversampled(ocfg, 2, u, v, w, vis, wt, correct=False)) < TOL
+    img_c = plan.image()[0].cpu().numpy()
+    assert rel_err(img_c, oracle.image_oversampled(ocfg, 2, u, v, w, vis, wt)) < TOL
+    dU = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    got = plan.kernel_grad(dev(dU[None])).cpu().numpy()
+    ref = oracle.kernel_grad_oversampled(ocfg, 2, u, v, w, vis, dU, wt)
+    assert np.abs(got - ref).max() < 1e-4 * np.abs(ref).max()

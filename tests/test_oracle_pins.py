@@ -595,6 +595,51 @@ def test_oversampled_image_within_half_band_aliasing_bound():
     assert err.max() < 2e-3 * np.abs(d).max() and err.max() * 20 < plain.max()
 
 
+def test_oversampled_degrid_is_adjoint_dot_product():
+    """<y, A_os x> = <A_os^H y, x> for the oversampled image (crop of the 2N-grid image)
+    and its adjoint (zero-pad, then the 2N-grid degridding), with and without the grid
+    correction."""
+    N, fov = 32, 0.1
+    rng = np.random.default_rng(23)
+    u, v, w = synth.disk_uvw(150, 0.45 * N / fov, 200.0, rng)
+    wt = rng.uniform(0.5, 2.0, 150).astype(np.float32)
+    x = synth.random_visibilities(150, rng)
+    cfg = OracleConfig(N, fov, 3, -200.0, 200.0, 7)
+    y = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    for corr in (True, False):
+        Ax = oracle.image_oversampled(cfg, 2, u, v, w, x, wt, correct=corr)
+        Ahy = oracle.degrid_oversampled(cfg, 2, u, v, w, x, y, wt, correct=corr)
+        lhs = np.vdot(y, Ax)
+        rhs = np.vdot(Ahy, x.astype(complex))
+        assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # a zero image has a zero adjoint (nothing outside the N x N image enters)
+    assert np.all(oracle.degrid_oversampled(cfg, 2, u, v, w, x, np.zeros((N, N)), wt) == 0)
+
+
+def test_oversampled_kernel_grad_finite_differences():
+    N, fov, W = 32, 0.1, 8
+    L = W * 4 + 1
+    rng = np.random.default_rng(24)
+    u, v, w = synth.disk_uvw(50, 0.45 * N / fov, 200.0, rng)
+    vis = synth.random_visibilities(50, rng)
+    tab = np.exp(-np.linspace(-W / 2, W / 2, L) ** 2 / (2 * 0.925**2))
+    cfg = OracleConfig(N, fov, 3, -200.0, 200.0, W, "table", 0.0, tab)
+    dU = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    g = oracle.kernel_grad_oversampled(cfg, 2, u, v, w, vis, dU)
+
+    def loss(t):
+        c = OracleConfig(N, fov, 3, -200.0, 200.0, W, "table", 0.0, t)
+        return np.real(np.vdot(dU, oracle.image_oversampled(c, 2, u, v, w, vis, correct=False)))
+
+    h = 1e-3
+    for i in (0, 5, L // 2, L - 3, L - 1):
+        tp, tm = tab.copy(), tab.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)  # exact for a loss quadratic in the table
+        assert abs(fd - g[i]) < 1e-8 * max(1.0, np.abs(g).max())
+
+
 # ------------------------------------------------------------------------------------------
 # inputs by row and channel (the layout of the LOFAR datasets of section 4)
 # ------------------------------------------------------------------------------------------
