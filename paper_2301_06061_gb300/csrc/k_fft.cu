@@ -371,6 +371,21 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
   cp_async_wait<0>();
 }
 
+// mbarrier and TMA helpers of the TMA-fed kernels
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_tile3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                                uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
 // ---------------------------------------------------------------------------------
 // phase screen helpers (K-P)
 //
@@ -772,25 +787,14 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
 // ---------------------------------------------------------------------------------
 constexpr int kColsBRing = 3;
 
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_tile3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
-                                                uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
-      : "memory");
-}
-
 template <int LA, bool FP64S, bool CROP>
 __global__ void __launch_bounds__(LA / 16 * kCB, LA == 128 ? 3 : 6)
 k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, Tw tw, int n, ScreenCtx sc,
              float2 *__restrict__ image, float2 *__restrict__ comp, int flags, int n_img_arg, int crop_arg,
-             unsigned long long *__restrict__ err, unsigned long long wait_ns) {
+             unsigned long long *__restrict__ err, unsigned long long wait_ns, int first_lo, int last_hi) {
+  // an image starts its sum in this call if its first plane is at or after first_lo (p0,
+  // or below every plane when the call starts the requested range) and finishes it if its
+  // last plane is before last_hi (p1, or above every plane when the call ends the range)
   const int n_img = CROP ? n_img_arg : n, crop = CROP ? crop_arg : 0;  // as in k_cols_b_acc
   constexpr int EPT = 16, TPL = LA / EPT, THREADS = TPL * kCB, R1 = LA / 16;
   static_assert(num_stages(LA, EPT) == 2 && stage_radix(LA, EPT, 1) == R1, "two stages");
@@ -929,8 +933,8 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
       }
     }
     if (failed) break;
-    const bool first_any = img * n_w >= p0 || (flags & ACC_RANGE_START);
-    const bool last_any = (img + 1) * n_w <= p1 || (flags & ACC_RANGE_END);
+    const bool first_any = img * n_w >= first_lo;
+    const bool last_any = (img + 1) * n_w <= last_hi;
     float2 *im = image + (size_t)img * n_img * n_img;
     float2 *cp = comp ? comp + (size_t)img * n_img * n_img : nullptr;
 #pragma unroll
@@ -1199,7 +1203,8 @@ static void launch_cols_b_variant(wst_plan_s *p, const float2 *planes, int p0, i
     if (plane_tile_map(&map, planes, p->n, p1 - p0, LA))
       k_cols_b_tma<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
           map, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop,
-          p->W_.counters + CNT_ERROR, p->wait_ns);
+          p->W_.counters + CNT_ERROR, p->wait_ns, (flags & ACC_RANGE_START) ? -1 : p0,
+          (flags & ACC_RANGE_END) ? 0x7FFFFFFF : p1);
     else
       k_cols_b16<LA, FP64S, CROP><<<grd, LA / 16 * kCB, 0, p->stream>>>(
           planes, p0, p1, p->n_w, tw_of(p), p->n, screen_ctx(p), image, comp, flags, p->n_img, p->crop);
