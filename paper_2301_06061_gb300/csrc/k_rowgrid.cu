@@ -100,19 +100,19 @@ constexpr int kFixedBinCap = 8192;
 template <int N>
 constexpr bool kFixedRows = N >= kFixedMinN;
 
-// one tap into the planar row: float atomics, or (FIXED) the value in units of the
-// row's quantum (qscale = 1/delta) as an integer atomic; ovf turns negative if the
-// conversion saturated or the cell's partial sum wrapped around
+// one tap into the planar row: float atomics, or (FIXED) the tap already in units of the
+// row's quantum (the record's value was scaled by 1/delta once), converted and added as
+// an integer atomic; ovf turns negative if the cell's partial sum wrapped around (the
+// returned old value and the new sum have signs no in-range sum can give).  Saturated
+// conversions are excluded per record (grid_row), not per tap.
 template <bool FIXED>
-__device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re, float im, float qscale, int &ovf) {
+__device__ __forceinline__ void add_tap(float *sre, float *sim, int c, float re, float im, int &ovf) {
   if constexpr (FIXED) {
-    const float fr = re * qscale, fi = im * qscale;
-    const int xr = __float2int_rn(fr), xi = __float2int_rn(fi);
+    const int xr = __float2int_rn(re), xi = __float2int_rn(im);
     const int o1 = atomicAdd(reinterpret_cast<int *>(sre) + c, xr);
     const int o2 = atomicAdd(reinterpret_cast<int *>(sim) + c, xi);
-    // a tap outside the int32 range (saturated conversion) or a partial sum that wrapped
-    ovf |= ((o1 ^ (o1 + xr)) & (xr ^ (o1 + xr))) | ((o2 ^ (o2 + xi)) & (xi ^ (o2 + xi))) |
-           (fmaxf(fabsf(fr), fabsf(fi)) >= 0x1p31f ? -1 : 0);
+    const int s1 = o1 + xr, s2 = o2 + xi;
+    ovf |= ((o1 ^ s1) & (xr ^ s1)) | ((o2 ^ s2) & (xi ^ s2));
   } else {
     atomicAdd(&sre[c], re);
     atomicAdd(&sim[c], im);
@@ -128,10 +128,13 @@ __device__ __forceinline__ void cp_async16_rg(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+// With FIXED, qscale = 1/delta and gmax the largest |kernel value|: a record whose scaled
+// value times gmax comes within 0.2% of 2^31 (a margin for the rounding of the taps)
+// could saturate a conversion, and sends the row to float atomics like a wrapped sum.
 template <int N, int WT, bool FIXED>
 __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__restrict__ rec,
                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
-                                        float qscale, RecHead *stg, int stg_stride) {
+                                        float qscale, float gmax, RecHead *stg, int stg_stride) {
   constexpr int TPR = RowCfg<N>::TPR;
   int ovf = 0;
   const uint32_t s_end = bnd[d_lo + 1];
@@ -155,9 +158,11 @@ __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__
       float g[WT];
       x_taps<WT>(kp, rec_gx(r), q, g);
       const int i0 = rec_i0(r);
-      const float vre = r.vre * gy, vim = r.vim * gy;
+      const float gq = FIXED ? gy * qscale : gy;
+      const float vre = r.vre * gq, vim = r.vim * gq;
+      if (FIXED && fmaxf(fabsf(vre), fabsf(vim)) * gmax >= 0x1.ffp30f) ovf = -1;
 #pragma unroll
-      for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], qscale, ovf);
+      for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], ovf);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else {
@@ -169,9 +174,12 @@ __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__
       const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
       const float gx = rec_gx(r);
       const int i0 = rec_i0(r);
+      const float gq = FIXED ? gy * qscale : gy;
+      const float vre = r.vre * gq, vim = r.vim * gq;
+      if (FIXED && fmaxf(fabsf(vre), fabsf(vim)) * gmax >= 0x1.ffp30f) ovf = -1;
       for (int a = 0; a < W; ++a) {
-        const float g = gy * kernel_eval(kp, (float)a - kp.half + gx);
-        add_tap<FIXED>(sre, sim, i0 + a, r.vre * g, r.vim * g, qscale, ovf);
+        const float g = kernel_eval(kp, (float)a - kp.half + gx);
+        add_tap<FIXED>(sre, sim, i0 + a, vre * g, vim * g, ovf);
       }
     }
   }
@@ -185,7 +193,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
                                              const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
                                              const KernelParams &kp, float2 *__restrict__ orow,
                                              const float2 *twt, int jt, const float2 *__restrict__ rowbound,
-                                             float g2, RecHead *stg, int stg_stride) {
+                                             float gmax, RecHead *stg, int stg_stride) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -206,7 +214,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   // the same decision and quantum in every thread of the row
   const uint32_t cnt = nonempty ? bnd[d_lo + 1] - bnd[0] : 0u;
   const float mmax = mb.x, mtot = mb.y;
-  const float bound = mmax * g2;
+  const float bound = mmax * (gmax * gmax);
   // n_eff: the busiest bin's magnitude in units of the row's mean per visibility-row
   const float n_eff = mmax * (float)cnt * (1.0f + (float)(W - 1) / (float)kBinCols) / fmaxf(mtot, 0x1p-126f);
   const bool fixed = kFixedRows<N> && nonempty && cnt < (1u << 30) && bound >= 0x1p-90f && bound <= 0x1p+100f &&
@@ -217,8 +225,8 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   bool fx = fixed;
   int ovf = 0;
   if (nonempty) {
-    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit), stg, stg_stride);
-    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, stg, stg_stride);
+    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit), gmax, stg, stg_stride);
+    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride);
   }
   bool redo = false;  // a tap or a partial sum left the int32 range: accumulate in float
   if constexpr (kFixedRows<N>) redo = __syncthreads_or(ovf < 0);
@@ -226,7 +234,7 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   if (redo) {
     zero_row<N>(srow, jt);
     __syncthreads();
-    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, stg, stg_stride);
+    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride);
     fx = false;
     __syncthreads();
   }
@@ -310,7 +318,6 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
   }
   __syncthreads();
   const float gmax = __uint_as_float(s_gmax);
-  const float g2 = gmax * gmax;
   const long long total = (long long)np * N;
   const int W = WT > 0 ? WT : kp.support;
   auto row_empty = [&](long long item) {
@@ -351,7 +358,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const long long item = base + (e >> 1);
         const int pl = (int)(item / N), q = (int)(item % N);
         grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
-                                 out + ((int64_t)pl * N + q) * N, twt, jt, rowbound, g2, stg, stg_stride);
+                                 out + ((int64_t)pl * N + q) * N, twt, jt, rowbound, gmax, stg, stg_stride);
       }
     }
   } else {
@@ -369,7 +376,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
       grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt,
-                               rowbound, g2, stg, stg_stride);
+                               rowbound, gmax, stg, stg_stride);
     }
   }
 }
