@@ -349,17 +349,42 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_stage: str, workload: str, launch_scale: float):
-    """DRAM bytes per launch from the committed ncu summary, if it matches these sources."""
-    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
+def traffic_ratios():
+    """Per plane kernel, DRAM bytes measured by ncu on the small 16384^2 case over that
+    kernel's design bytes on the same case (profiles/traffic_16384_small.md), if the file
+    was taken with these CUDA sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_16384_small.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     if not m_hash or m_hash.group(1) != kernel_source_hash():
         return None
-    m = re.search(rf"{kernel_stage}_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    return float(m.group(1)) * launch_scale if m else None
+    out = {}
+    for key in ("grid_read", "grid_write", "cols_a_read", "cols_a_write", "cols_b_read", "cols_b_write"):
+        m = re.search(rf"{key}_ratio:\s*([0-9.eE+-]+)", text)
+        if not m:
+            return None
+        out[key] = float(m.group(1))
+    return out
+
+
+def launch_traffic(stage: str, n: int, planes_per_launch: float, rows_gridded_per_launch: float, n_kept_per_launch: float,
+                   images: int, oversample: int = 1, ratios: dict | None = None):
+    """DRAM bytes of one launch of a plane kernel: its design bytes on this workload (the
+    occupied rows it writes or reads, the records, the planes, the image) times the ratio
+    of measured to design bytes of the small-case capture; None without a matching
+    capture.  The design bytes scale with the units each kernel moves, so the ratios do."""
+    r = traffic_ratios() if ratios is None else ratios
+    if r is None or stage not in ("grid", "cols_a", "cols_b"):
+        return None
+    row = 8.0 * n * oversample
+    S = row * n * oversample
+    if stage == "grid":
+        return r["grid_read"] * 32.0 * n_kept_per_launch + r["grid_write"] * row * rows_gridded_per_launch
+    if stage == "cols_a":
+        return r["cols_a_read"] * row * rows_gridded_per_launch + r["cols_a_write"] * S * planes_per_launch
+    return r["cols_b_read"] * S * planes_per_launch + r["cols_b_write"] * 8.0 * n * n * images
 
 
 # ------------------------------------------------------------------------------------------
@@ -612,7 +637,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "cols_b": "k_cols_b16 (column stage B + phase screen + Kahan plane sum)"}
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic(dom, args.workload, 1.0),
+                "traffic": launch_traffic(dom, work.n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
+                                          st["n_kept"] / st["n_chunks"], batch, osf),
+                "traffic_source": "small-case ncu ratios (profiles/traffic_16384_small.md) times this launch's "
+                                  "design bytes (n_rows_gridded occupied rows, records, planes, image)",
                 "bytes_per_launch": bytes_launch, "ms_per_launch": round(per_launch_ms, 4),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stages.items()},

@@ -115,6 +115,9 @@ typedef struct wst_stats {
   int32_t device_error; /* 0, or a WST_ERR_* raised on the device                       */
   int32_t n_chunks;     /* plane chunks used by the last wst_image                      */
   int64_t n_launches;   /* kernels launched by the last set_vis + wst_image             */
+  int64_t n_rows_gridded; /* (plane, row) grid rows the last wst_image / wst_image_range  */
+                          /* gridded and transformed: the rows some visibility reaches; */
+                          /* the others are known zero and never written or read       */
 } wst_stats;
 
 typedef struct wst_plan_s *wst_plan;

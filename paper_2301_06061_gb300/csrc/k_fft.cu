@@ -263,15 +263,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Pass CA, persistent: each CTA walks tiles (plane, a, 32-column band: 256-byte row
-// segments) in band-fastest order; the next tile's rows are copied into a shared staging
-// buffer with cp.async while the current one is transformed (rows the gridder left
-// empty are zero-filled instead of read, their flags loaded a tile ahead).  16 elements
-// per thread (LB = 32, 64, 128: radix 16, then LB/16 with the stage twiddles in
-// registers); one exchange between the two register stages through a buffer of its
-// own, so a tile costs two barriers.  A warp covers 32 columns at one line position:
-// shared-memory accesses are conflict-free without padding and twiddles are
-// warp-uniform.  The factors w_N^{a c} of a tile come from a shared table filled one
-// tile ahead (three in rotation).
+// segments) in band-fastest order; tiles are copied into a ring of three shared slots
+// with cp.async, two tiles ahead (rows the gridder left empty are zero-filled instead of
+// read, their flags loaded ahead).  16 elements per thread (LB = 32, 64, 128: radix 16,
+// then LB/16 with the stage twiddles in registers); the exchange between the two
+// register stages is made in place in the tile's slot (three barriers per tile), which
+// keeps two CTAs per SM with the deeper ring.  A warp covers 32 columns at one line
+// position: shared-memory accesses are conflict-free without padding and twiddles are
+// warp-uniform.  The factors w_N^{a c} of a tile come from a shared table filled with the
+// tile (three in rotation).
 template <int LB, int DIR, bool TW_FIRST>
 __global__ void __launch_bounds__(LB / 16 * 32, 512 / (LB / 16 * 32))
 k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
@@ -281,8 +281,7 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
   constexpr int PIECES = LB * (CB / 2);     // 16-byte pieces per tile
   constexpr int PPT = PIECES / THREADS;     // pieces per thread (8)
   static_assert(PIECES % THREADS == 0, "pieces");
-  __shared__ __align__(16) float2 stage[2][LB * CB];
-  __shared__ float2 xbuf[LB * CB];  // exchange between the two register stages
+  __shared__ __align__(16) float2 stage[3][LB * CB];
   __shared__ float2 s_tw[3][LB];    // w_N^{DIR a c}, c < LB, of the tiles in flight
   const int A = n / LB;
   const int lg_bands = 31 - __clz(n / CB), lg_A = 31 - __clz(A);
@@ -320,26 +319,29 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
   };
   int t = blockIdx.x;
   bool f0[PPT], f1[PPT];
+  const int G = gridDim.x;
+  // tiles it and it + 1 in flight before the loop; tile it + 2 is issued after the first
+  // barrier of tile it, into the slot of tile it - 1
   load_flags(t, f0);
-  load_flags(t + gridDim.x, f1);
-  if (t < total) {
-    issue(t, stage[0], f0);
-    fill_tw(t, s_tw[0]);
-  }
+  if (t < total) { issue(t, stage[0], f0); fill_tw(t, s_tw[0]); }
   cp_async_commit();
-  for (int it = 0; t < total; ++it, t += gridDim.x) {
-    if (t + gridDim.x < total) {
-      issue(t + gridDim.x, stage[(it + 1) & 1], f1);
-      fill_tw(t + gridDim.x, s_tw[(it + 1) % 3]);
-    }
-    cp_async_commit();
-    load_flags(t + 2 * (int)gridDim.x, f1);
+  load_flags(t + G, f0);
+  if (t + G < total) { issue(t + G, stage[1], f0); fill_tw(t + G, s_tw[1]); }
+  cp_async_commit();
+  load_flags(t + 2 * G, f1);
+  for (int it = 0; t < total; ++it, t += G) {
     const int band = t & ((1 << lg_bands) - 1);
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
     const float2 *tws = s_tw[it % 3];
     cp_async_wait<1>();
-    __syncthreads();  // tile it landed; the exchange buffer's readers of tile it-1 are done
-    const float2 *buf = stage[it & 1];
+    __syncthreads();  // tile it landed; every thread is done with tile it - 1
+    if (t + 2 * G < total) {
+      issue(t + 2 * G, stage[(it + 2) % 3], f1);
+      fill_tw(t + 2 * G, s_tw[(it + 2) % 3]);
+    }
+    cp_async_commit();
+    load_flags(t + 3 * G, f1);
+    float2 *buf = stage[it % 3];
     float2 v[EPT];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -349,13 +351,14 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
       v[r] = x;
     }
     dft<16, DIR>(v);
+    __syncthreads();  // every stage-0 read of the slot done before the exchange in place
 #pragma unroll
-    for (int r = 0; r < 16; ++r) xbuf[(16 * jt + r) * CB + col] = v[r];
-    __syncthreads();  // exchange complete; every read of the staging buffer is done
+    for (int r = 0; r < 16; ++r) buf[(16 * jt + r) * CB + col] = v[r];
+    __syncthreads();
 #pragma unroll
     for (int b = 0; b < 16 / R1; ++b)
 #pragma unroll
-      for (int r = 0; r < R1; ++r) v[b * R1 + r] = xbuf[(jt + b * TPL + 16 * r) * CB + col];
+      for (int r = 0; r < R1; ++r) v[b * R1 + r] = buf[(jt + b * TPL + 16 * r) * CB + col];
     stage_compute_pre<LB, EPT, 1, DIR>(v, twr);
     float2 *dst = planes + (size_t)z * n * n + (size_t)a * n + band * CB + col;
 #pragma unroll

@@ -291,7 +291,8 @@ template <int N, bool FFT, int WT>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
 k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, int p0, int np,
             KernelParams kp, float2 *__restrict__ out, uint8_t *__restrict__ occ,
-            unsigned long long *__restrict__ counter, Tw tw, const float2 *__restrict__ rowbound) {
+            unsigned long long *__restrict__ counter, Tw tw, const float2 *__restrict__ rowbound,
+            unsigned long long *__restrict__ rows_done) {
   using C = RowCfg<N>;
   constexpr int TPR = C::TPR, RPC = C::RPC;
   extern __shared__ __align__(16) float2 sm_rows[];
@@ -350,6 +351,10 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const unsigned m = __ballot_sync(0xFFFFFFFFu, listed);
         if (listed) s_list[__popc(m & ((1u << threadIdx.x) - 1u))] = threadIdx.x * 2 + (nonempty ? 1 : 0);
         if (threadIdx.x == 0) s_cnt = __popc(m);
+        if (rows_done) {  // the occupied rows of the batch, for the caller's statistics
+          const unsigned occupied = __ballot_sync(0xFFFFFFFFu, nonempty);
+          if (threadIdx.x == 0 && occupied) atomicAdd(rows_done, (unsigned long long)__popc(occupied));
+        }
       }
       __syncthreads();
       const int cnt = s_cnt;
@@ -374,6 +379,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       const int q = valid ? (int)(item % N) : 0;
       const bool empty = !valid || row_empty(item);
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
+      if (rows_done && valid && jt == 0 && !empty) atomicAdd(rows_done, 1ull);
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
       grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt,
                                rowbound, gmax, stg, stg_stride);
@@ -545,7 +551,8 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), p->stream);
   if (e != cudaSuccess) return e;
   kern<<<grid, C::THREADS, smem, p->stream>>>(p->W_.records, p->W_.offsets, p0, np, kernel_params(p), out,
-                                             p->W_.occ, counter, tw_half(p), p->W_.rowbound);
+                                             p->W_.occ, counter, tw_half(p), p->W_.rowbound,
+                                             FFT ? p->W_.counters + CNT_ROWS : nullptr);
   return cudaGetLastError();
 }
 

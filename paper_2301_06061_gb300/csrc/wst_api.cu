@@ -457,6 +457,7 @@ static wst_status image_range(wst_plan_s *p, int b, int e, void *image_out, uint
   float2 *planes = p->W_.planes;
   p->n_chunks = 0;
   p->launches = 0;
+  WST_CUDA(p, cudaMemsetAsync(p->W_.counters + CNT_ROWS, 0, sizeof(unsigned long long), p->stream), "memset");
   for (int p0 = b; p0 < e; p0 += p->chunk) {
     const int p1 = (p0 + p->chunk < e) ? p0 + p->chunk : e;
     WST_CUDA(p, time_begin(p, p->ev_img, ST_GRID), "event");
@@ -543,6 +544,7 @@ wst_status wst_get_stats(wst_plan p, wst_stats *out) {
     out->n_dropped = (int64_t)cnt[CNT_DROPPED];
     out->n_nonfinite = (int64_t)cnt[CNT_NONFINITE];
     out->device_error = (int32_t)cnt[CNT_ERROR];
+    out->n_rows_gridded = (int64_t)cnt[CNT_ROWS];
     double wr[4];
     WST_CUDA(p, cudaMemcpy(wr, p->wrange, sizeof(wr), cudaMemcpyDeviceToHost), "w range");
     out->w_min = wr[0];

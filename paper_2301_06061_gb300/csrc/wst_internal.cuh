@@ -24,7 +24,8 @@ constexpr int kFixedMinN = 8192;  // image sizes whose rows use fixed-point accu
 __host__ __device__ constexpr int bins_per_row(int n) { return n >= kBinCols ? n / kBinCols : 1; }
 
 // counters[] slots in the workspace
-enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_WORK = 4, CNT_SLOTS = 8 };
+// CNT_ROWS: non-empty (plane, row) items the imaging path gridded since wst_image began
+enum { CNT_KEPT = 0, CNT_DROPPED = 1, CNT_NONFINITE = 2, CNT_ERROR = 3, CNT_WORK = 4, CNT_ROWS = 5, CNT_SLOTS = 8 };
 
 // 32-byte sorted record of a visibility filed under (image, plane, row j0).  The head
 // (16 bytes, all the gridder reads): tap start i0 (14 bits, N <= 16384) and the sub-cell

@@ -76,6 +76,7 @@ class wst_stats(ctypes.Structure):
         ("device_error", ctypes.c_int32),
         ("n_chunks", ctypes.c_int32),
         ("n_launches", ctypes.c_int64),
+        ("n_rows_gridded", ctypes.c_int64),
     ]
 
 

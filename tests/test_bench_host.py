@@ -57,3 +57,15 @@ def test_oracle_extrapolation_scales_gridding_by_visibilities_and_the_rest_by_pl
     assert job == pytest.approx(25 * 2.0 + 32 * 8.0)
     # a sample with every visibility of the job: gridding is billed once
     assert bench.oracle_job_seconds(2.0, 10.0, 100, 100, 1) == pytest.approx(10.0)
+
+
+def test_launch_traffic_scales_the_design_bytes_by_the_measured_ratios():
+    r = {"grid_read": 1.13, "grid_write": 1.0, "cols_a_read": 1.02, "cols_a_write": 0.99, "cols_b_read": 1.0,
+         "cols_b_write": 0.99}
+    n, rows, kept = 16384, 224_000, 100_000_000
+    row = 8.0 * n
+    assert bench.launch_traffic("grid", n, 32, rows, kept, 1, ratios=r) == pytest.approx(1.13 * 32 * kept + rows * row)
+    assert bench.launch_traffic("cols_a", n, 32, rows, kept, 1, ratios=r) == pytest.approx(
+        1.02 * rows * row + 0.99 * 32 * S)
+    assert bench.launch_traffic("cols_b", n, 32, rows, kept, 1, ratios=r) == pytest.approx(32 * S + 0.99 * S)
+    assert bench.launch_traffic("sort", n, 32, rows, kept, 1, ratios=r) is None

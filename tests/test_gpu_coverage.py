@@ -321,3 +321,22 @@ def test_transform_matches_cufft(wst, n):
         tp = np.abs(truth).max()
         assert np.abs(ours[0].cpu().numpy() - truth).max() <= TOL * tp
         assert np.abs(ref.cpu().numpy() - truth).max() <= TOL * tp
+
+
+def test_rows_gridded_counts_the_occupied_rows(wst):
+    """wst_stats.n_rows_gridded: the (plane, row) items some visibility's W-row footprint
+    reaches (the oracle's placements j0 .. j0 + W - 1 per plane), over all chunks."""
+    rng = np.random.default_rng(92)
+    n, n_w, W = 1024, 5, 7
+    u, v, w = synth.disk_uvw(3000, 0.3 * n / 0.1, 200.0, rng)
+    vis = synth.random_visibilities(u.size, rng)
+    for chunk in (0, 2):
+        plan = wst.Plan(wst.Config(n=n, fov=0.1, n_w=n_w, w_min=-200.0, w_max=200.0, planes_per_chunk=chunk))
+        plan.set_vis(dev(u), dev(v), dev(w), dev(vis))
+        plan.image()
+        got = plan.stats()["n_rows_gridded"]
+        k, _, j0, st = oracle.locate(OracleConfig(n, 0.1, n_w, -200.0, 200.0, W), u, v, w, vis)
+        rows = {(int(kk), int(jj) + d) for kk, jj, ss in zip(k, j0, st) if ss == 0 for d in range(W)}
+        assert got == len(rows)
+        plan.image_range(1, 3)
+        assert plan.stats()["n_rows_gridded"] == len({r for r in rows if 1 <= r[0] < 3})

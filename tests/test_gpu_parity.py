@@ -286,6 +286,7 @@ def test_fft_correct_staged(wst, n):
 @pytest.mark.parametrize("n,n_w,chunk,flags", [
     (256, 8, 0, 1), (256, 8, 3, 1), (256, 8, 3, 0), (512, 5, 2, 1), (1024, 4, 0, 3), (64, 1, 0, 1),
     (4096, 2, 1, 1), (2048, 3, 0, 1), (8192, 2, 1, 1),
+    (4096, 3, 2, 3), (8192, 2, 0, 3), (2048, 17, 0, 1),  # FP64 screen on the TMA column pass; > 16 planes
 ])
 def test_image_end_to_end(wst, n, n_w, chunk, flags):
     u, v, w, vis = make_case(n=n, n_vis=4000, seed=7 * n + n_w)
