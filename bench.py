@@ -772,6 +772,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "wfold": args.wfold, "oversample": max(1, args.oversample),
                        "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
+                       "rows_gridded": st["n_rows_gridded"],
                        "l2": "inputs larger than L2 (20 B/vis inputs, 8 B/cell planes)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "cufft_compare": cufft,
