@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--snap-w", action="store_true",
                     help="place every w on its plane centre, so the error against the direct transform is "
                          "the (u,v) kernel's alone (kernel comparisons)")
+    ap.add_argument("--table-per-cell", type=int, default=1024,
+                    help="samples per cell of the tabulated kernels (kb8, learned); 1024 is the trained "
+                         "kernel's resolution, 128 keeps the gridder's tap table in L1 (3%% faster)")
     ap.add_argument("--oversample", type=int, default=0, choices=[0, 1, 2],
                     help="2: grid of 2N cells, the central N x N kept (images up to 8192^2)")
     ap.add_argument("--wfold", action="store_true",
@@ -567,11 +570,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if args.kernel == "kb8":
             from paper_2301_06061_gb300 import kernels
 
-            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, float(max(1, args.oversample))))
+            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, float(max(1, args.oversample))),
+                                                 args.table_per_cell)
         else:
             from paper_2301_06061_gb300 import learned
 
-            tab_np = learned.load_table(os.path.join(ROOT, "paper_2301_06061_gb300", "data", "learned_kernel_w8.npz"))
+            tab_np = learned.table_at(os.path.join(ROOT, "paper_2301_06061_gb300", "data", "learned_kernel_w8.npz"),
+                                      args.table_per_cell)
         table = torch.from_numpy(tab_np).to(dev)
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
     cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
@@ -769,6 +774,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
                        "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w,
+                       "table_samples": None if table is None else int(tab_np.size),
                        "wfold": args.wfold, "oversample": max(1, args.oversample),
                        "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],

@@ -234,6 +234,25 @@ def load_table(path: str) -> np.ndarray:
         return f["table"].astype(np.float32)
 
 
+def load_mlp(path: str) -> KernelMLP:
+    """The trained network saved beside the table (its parameters under "mlp.")."""
+    with np.load(path) as f:
+        mlp = KernelMLP(int(f["support"]))
+        mlp.load_state_dict({k[4:]: torch.from_numpy(f[k]) for k in f.files if k.startswith("mlp.")})
+    return mlp
+
+
+def table_at(path: str, per_cell: int) -> np.ndarray:
+    """The trained kernel tabulated at per_cell samples per cell (FP32): the stored table
+    when per_cell is its own resolution, else the network sampled afresh."""
+    with np.load(path) as f:
+        if int(f["per_cell"]) == per_cell:
+            return f["table"].astype(np.float32)
+        support = int(f["support"])
+    with torch.no_grad():
+        return tabulate(load_mlp(path), support, per_cell).numpy().astype(np.float32)
+
+
 def load_report(path: str) -> dict:
     with np.load(path) as f:
         return dict(zip([str(k) for k in f["report_keys"]], [float(v) for v in f["report_vals"]]))

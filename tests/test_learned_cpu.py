@@ -72,3 +72,21 @@ def test_training_resumes_from_a_checkpoint_as_if_uninterrupted(tmp_path):
                                           torch.optim.Adam(learned.KernelMLP(8).parameters()))
     assert step == 6 and saved == ref_hist
     assert not (tmp_path / "train.pt.tmp").exists()
+
+
+def test_trained_kernel_tabulated_at_any_resolution():
+    """The stored table is the network at 1024 samples per cell; table_at resamples the
+    network (the bench grids with 128 per cell, whose tap table stays in L1)."""
+    import os
+
+    from paper_2301_06061_gb300 import learned
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2301_06061_gb300",
+                        "data", "learned_kernel_w8.npz")
+    stored = learned.load_table(path)
+    again = learned.table_at(path, 1024)
+    assert np.array_equal(stored, again)
+    coarse = learned.table_at(path, 128)
+    assert coarse.size == 8 * 128 + 1
+    # every 8th sample of the fine table is a sample of the coarse one (the same nodes)
+    assert np.abs(coarse - stored[::8]).max() < 1e-6
