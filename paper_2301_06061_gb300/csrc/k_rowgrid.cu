@@ -53,13 +53,15 @@ __device__ __forceinline__ void zero_row(float2 *srow, int jt) {
 
 // The W x-taps G(a - W/2 + g_x), a = 0 .. W-1.  For the Gaussian, three exponentials
 // instead of W: with t = g_x - W/2, G(t + a + 1) / G(t + a) = R q^a, R = exp(-(2t + 1) c),
-// q = exp(-2c), c = 1/(2 sigma^2).
+// q = exp(-2c), c = 1/(2 sigma^2); each exponential is a power of two, exp(-y c) =
+// 2^(-y c log2 e), with c log2 e rounded once from FP64 (the FP32 argument carries the
+// same rounding as with exp).
 template <int WT>
 __device__ __forceinline__ void x_taps(const KernelParams &kp, float gx, float q, float (&g)[WT]) {
   if (kp.kind == WST_KERNEL_GAUSS) {
     const float t = gx - kp.half;
-    float ga = expf(-t * t * kp.inv2s2);
-    float ra = expf(-(2.0f * t + 1.0f) * kp.inv2s2);
+    float ga = exp2f(-t * t * kp.l2c);
+    float ra = exp2f(-(2.0f * t + 1.0f) * kp.l2c);
 #pragma unroll
     for (int a = 0; a < WT; ++a) {
       g[a] = ga;
@@ -139,22 +141,29 @@ __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__
   int ovf = 0;
   const uint32_t s_end = bnd[d_lo + 1];
   if constexpr (WT > 0) {
-    const float q = expf(-2.0f * kp.inv2s2);
-    // this thread's record heads are copied into its own two shared slots one record
-    // ahead (cp.async), so the next load is in flight while a record is gridded
+    const float q = exp2f(-2.0f * kp.l2c);
+    // this thread's record heads are copied into its own three shared slots two records
+    // ahead (cp.async), so two loads are in flight while a record is gridded
     const uint32_t slot0 = (uint32_t)__cvta_generic_to_shared(stg);
-    const uint32_t slot1 = (uint32_t)__cvta_generic_to_shared(stg + stg_stride);
+    const uint32_t sstep = (uint32_t)(stg_stride * sizeof(RecHead));
     uint32_t s = bnd[0] + jt;
     if (s < s_end) cp_async16_rg(slot0, rec + s);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int k = 0; s < s_end; ++k, s += TPR) {
-      if (s + TPR < s_end) cp_async16_rg((k & 1) ? slot0 : slot1, rec + s + TPR);
+    if (s + TPR < s_end) cp_async16_rg(slot0 + sstep, rec + s + TPR);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int i = 0;  // the thread's records come in increasing order, so do their buckets
+    int cur = 0, nxt = 2;  // slot of this record, slot of the one two ahead
+    for (; s < s_end; s += TPR) {
+      if (s + 2 * TPR < s_end) cp_async16_rg(slot0 + nxt * sstep, rec + s + 2 * TPR);
       asm volatile("cp.async.commit_group;" ::: "memory");
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-      const RecHead r = (k & 1) ? stg[stg_stride] : stg[0];
-      int i = d_lo;
-      while (s < bnd[i]) --i;  // the last row starting at or before the record
-      const float gy = kernel_eval(kp, (float)(d_lo - i) - kp.half + rec_gy(r));
+      asm volatile("cp.async.wait_group 2;" ::: "memory");
+      const RecHead r = stg[cur * stg_stride];
+      cur = cur == 2 ? 0 : cur + 1;
+      nxt = nxt == 2 ? 0 : nxt + 1;
+      while (i < d_lo && bnd[i + 1] <= s) ++i;  // the last row starting at or before the record
+      // the record's row offset keeps y in [-W/2, W/2): no range test
+      const float y = (float)(d_lo - i) - kp.half + rec_gy(r);
+      const float gy = kp.kind == WST_KERNEL_GAUSS ? exp2f(-y * y * kp.l2c) : kernel_eval(kp, y);
       float g[WT];
       x_taps<WT>(kp, rec_gx(r), q, g);
       const int i0 = rec_i0(r);
@@ -302,7 +311,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
   const int rl = threadIdx.x / TPR, jt = threadIdx.x % TPR;
   float2 *srow = sm_rows + rl * C::PADL;
   float2 *twt = sm_rows + RPC * C::PADL;  // twiddle tables (visible after the first barrier)
-  // two record-head slots per thread after the tables
+  // three record-head slots per thread after the tables
   RecHead *stg = reinterpret_cast<RecHead *>(twt + (FFT ? line_table_size<N, C::EPT, TPR>() : 0)) + threadIdx.x;
   const int stg_stride = C::THREADS;
   if constexpr (FFT) fill_line_tables<N, C::EPT, TPR>(twt, tw);
@@ -521,11 +530,10 @@ static Tw tw_half(const wst_plan_s *p) {
 
 template <class K>
 static cudaError_t persistent_grid(wst_plan_s *p, K kern, int threads, size_t smem, int &grid) {
-  cudaError_t e = cudaSuccess;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  // always raised to the request: the 48 KB default counts the kernel's static shared
+  // memory too, so a dynamic request just under 48 KB can already exceed it
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0, sms = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
@@ -543,7 +551,7 @@ static cudaError_t launch_grid_rows(wst_plan_s *p, int p0, int np, float2 *out) 
               : p->cfg.support == 7 ? k_grid_rows<N, FFT, 7>
               : p->cfg.support == 8 ? k_grid_rows<N, FFT, 8> : k_grid_rows<N, FFT, 0>;
   const size_t smem = sizeof(float2) * (C::RPC * C::PADL + (FFT ? line_table_size<N, C::EPT, C::TPR>() : 0)) +
-                      2 * C::THREADS * sizeof(RecHead);
+                      3 * C::THREADS * sizeof(RecHead);
   int grid = 0;
   cudaError_t e = persistent_grid(p, kern, C::THREADS, smem, grid);
   if (e != cudaSuccess) return e;

@@ -13,6 +13,7 @@ KernelParams kernel_params(const wst_plan_s *p) {
   k.half = 0.5f * (float)p->W;
   double s = p->cfg.kparam;
   k.inv2s2 = (k.kind == WST_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * s * s)) : 0.0f;
+  k.l2c = (k.kind == WST_KERNEL_GAUSS) ? (float)(1.4426950408889634 / (2.0 * s * s)) : 0.0f;
   k.beta = (k.kind == WST_KERNEL_ES) ? (float)s : 0.0f;
   k.two_over_w = 2.0f / (float)p->W;
   k.table = p->ktable;

@@ -68,6 +68,7 @@ struct KernelParams {
   int support;     // W
   float half;      // W/2
   float inv2s2;    // GAUSS: 1/(2 sigma^2)
+  float l2c;       // GAUSS: log2(e)/(2 sigma^2), so that G(x) = 2^(-x^2 l2c)
   float beta;      // ES
   float two_over_w;
   const float *table;  // TABLE: device samples
