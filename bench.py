@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--table-per-cell", type=int, default=1024,
                     help="samples per cell of the tabulated kernels (kb8, learned); 1024 is the trained "
                          "kernel's resolution, 128 keeps the gridder's tap table in L1 (3%% faster)")
+    ap.add_argument("--image-n", type=int, default=0,
+                    help="image the central N pixels of the workload's field (FoV N/n, the same pixels) on "
+                         "its n-cell grid: oversampling n/N (e.g. 3276 of 4096: 1.25); 0 = the whole field")
     ap.add_argument("--oversample", type=int, default=0, choices=[0, 1, 2],
                     help="2: grid of 2N cells, the central N x N kept (images up to 8192^2)")
     ap.add_argument("--wfold", action="store_true",
@@ -153,7 +156,7 @@ def kernel_function(kernel: str, support: int, sigma: float, table):
 
 
 def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np.ndarray,
-                 n_offsets: int = 512, oversample: int = 1) -> np.ndarray:
+                 n_offsets: int = 512, oversample: float = 1) -> np.ndarray:
     """eps(a) = sup over sub-cell offsets g of |sum_taps G(t) e^{2 pi i nu t} / Ghat(nu) - 1|,
     t = tap - W/2 + g, nu = (a - n/2)/(oversample n): the relative error of one
     visibility's gridded, transformed and corrected contribution at pixel index a along
@@ -180,14 +183,16 @@ def kernel_error(kernel: str, support: int, sigma: float, table, n: int, idx: np
 
 
 def accuracy_block(torch, wst, work, plan_stats, d_u, d_v, d_w, d_vis, img, dev, n_pix: int, kernel: str,
-                   support: int, sigma: float, table, wfold: bool = False, oversample: int = 1, plan=None):
+                   support: int, sigma: float, table, wfold: bool = False, oversample: float = 1, plan=None,
+                   n_img: int = 0, fov_img: float = 0.0):
     """The image against the direct transform (GPU, float-float phases) at the brightest
     sources' pixels and at seeded random pixels, with the per-pixel bound
     B = sum|V| (min(2, 2 pi dmax |n - 1|) + e_a + e_b + e_a e_b) + 1e-5 peak, dmax the
     largest distance of a w from its plane centre and e the kernel error above.  With
     w-folding the real parts are compared (the folded image's real part is the dirty
-    image) and the plane offsets are those of |w|."""
-    n, fov = work.n, work.fov
+    image) and the plane offsets are those of |w|.  n_img, fov_img: the image's side and
+    field when they are not the workload's (an image cropped from the workload's grid)."""
+    n, fov = (n_img, fov_img) if n_img else (work.n, work.fov)
     sky = work.sky
     order = np.argsort(-sky.flux)[: n_pix // 2]
     sa = np.clip(np.rint(n // 2 + sky.l[order] * n / fov), 0, n - 1).astype(np.int64)
@@ -570,8 +575,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if args.kernel == "kb8":
             from paper_2301_06061_gb300 import kernels
 
-            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, float(max(1, args.oversample))),
-                                                 args.table_per_cell)
+            alpha = work.n / args.image_n if args.image_n else float(max(1, args.oversample))
+            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, alpha), args.table_per_cell)
         else:
             from paper_2301_06061_gb300 import learned
 
@@ -579,9 +584,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                       args.table_per_cell)
         table = torch.from_numpy(tab_np).to(dev)
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab_np.size))
-    cfg = wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
+    # the image: the whole field on n pixels (or 2n grid cells with --oversample 2), or
+    # with --image-n the central N pixels (field FoV N/n) on the workload's n-cell grid
+    if args.image_n:
+        if args.oversample == 2 or args.image_n % 2 or not 64 <= args.image_n <= work.n:
+            raise SystemExit("--image-n: an even N, 64 <= N <= the workload's n, without --oversample 2")
+        img_n, img_fov, grid_n, osf = args.image_n, work.fov * args.image_n / work.n, work.n, work.n / args.image_n
+    else:
+        img_n, img_fov, grid_n, osf = work.n, work.fov, 0, float(max(1, args.oversample))
+    cfg = wst.Config(n=img_n, fov=img_fov, n_w=work.n_w, w_min=work.w_min, w_max=work.w_max,
                      flags=wst.WST_FLAG_KAHAN | wst.WST_FLAG_TIMING | (wst.WST_FLAG_WFOLD if args.wfold else 0),
-                     planes_per_chunk=args.chunk, batch=batch, oversample=args.oversample,
+                     planes_per_chunk=args.chunk, batch=batch, oversample=args.oversample, grid_n=grid_n,
                      **kcfg)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_u, h_v, h_w = pin(work.u), pin(work.v), pin(work.w)
@@ -597,7 +610,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     plan = wst.Plan(cfg, device=dev)
     if table is not None:
         plan.set_kernel_table(table)
-    img = torch.empty((batch, work.n, work.n), dtype=torch.complex64, device=dev)
+    img = torch.empty((batch, img_n, img_n), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -633,8 +646,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dom = max(stages, key=stages.get)
     per_launch_ms = stages[dom] / (args.steps * launches_per_stage[dom])
     planes = batch * work.n_w
-    osf = max(1, args.oversample)
-    bytes_launch = stage_bytes(dom, work.n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf)
+    bytes_launch = stage_bytes(dom, img_n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf)
     peak, peak_src = load_peaks()
     achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     kernel_names = {"sort": "k_keys+k_scan+k_scatter+k_row_bounds", "grid": "k_grid_rows (gridding + row FFT)",
@@ -642,18 +654,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                     "cols_b": "k_cols_b16 (column stage B + phase screen + Kahan plane sum)"}
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": launch_traffic(dom, work.n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
+                "traffic": launch_traffic(dom, img_n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
                                           st["n_kept"] / st["n_chunks"], batch, osf),
                 "traffic_source": "small-case ncu ratios (profiles/traffic_16384_small.md) times this launch's "
                                   "design bytes (n_rows_gridded occupied rows, records, planes, image)",
                 "bytes_per_launch": bytes_launch, "ms_per_launch": round(per_launch_ms, 4),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stages.items()},
-                "stage_frac_of_hbm": {k: round(stage_bytes(k, work.n, planes, st["n_chunks"], batch, st["n_kept"],
+                "stage_frac_of_hbm": {k: round(stage_bytes(k, img_n, planes, st["n_chunks"], batch, st["n_kept"],
                                                            n_vis, osf) * launches_per_stage[k] /
                                                (v / args.steps * 1e-3) / 1e9 / peak, 4)
                                       for k, v in stages.items() if v > 0}}
-    roofline["step"] = step_roofline({k: v / args.steps for k, v in stages.items()}, work.n, planes,
+    roofline["step"] = step_roofline({k: v / args.steps for k, v in stages.items()}, img_n, planes,
                                      st["n_chunks"], batch, st["n_kept"], n_vis, osf, ms_step, peak)
 
     cufft = None
@@ -664,7 +676,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        h_img = torch.empty((batch, work.n, work.n), dtype=torch.complex64).pin_memory()
+        h_img = torch.empty((batch, img_n, img_n), dtype=torch.complex64).pin_memory()
         rows = work.rows_m is not None
         if rows:
             h_rows, h_scale = pin(work.rows_m), pin(work.chan_scale)
@@ -703,7 +715,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
         e2e_ms = timed(e2e_step)
         copy_ms = timed(copy_step)
-        d2h = int(8 * batch * work.n * work.n)
+        d2h = int(8 * batch * img_n * img_n)
         plain = {"value": round(job_mvis(world, n_vis, e2e_ms), 2), "unit": "Mvis/s",
                  "h2d_bytes_per_step": int(20 * n_vis), "d2h_bytes_per_step": d2h,
                  "ms_per_step": round(e2e_ms, 3),
@@ -734,7 +746,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         sigma = kcfg.get("kparam", 0.0)
         acc = accuracy_block(torch, wst, work, st, d_u, d_v, d_w, d_vis, img, dev, args.dft_pixels,
                              args.kernel, cfg.support, sigma, None if table is None else tab_np, args.wfold,
-                             max(1, args.oversample), plan=plan)
+                             osf, plan=plan, n_img=img_n, fov_img=img_fov)
         if not args.snap_w and not args.wfold:
             # the same visibilities with every w moved to its plane's centre: the error
             # against the direct transform is then the (u, v) kernel's alone
@@ -742,16 +754,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             k = torch.clamp(torch.floor((d_w.double() - lo) * (work.n_w / (hi - lo))), 0, work.n_w - 1)
             d_ws = (lo + (k + 0.5) * (hi - lo) / work.n_w).float()
             plan.close()  # its workspace is no longer needed
-            plan = wst.Plan(wst.Config(n=work.n, fov=work.fov, n_w=work.n_w, w_min=lo, w_max=hi,
+            plan = wst.Plan(wst.Config(n=img_n, fov=img_fov, n_w=work.n_w, w_min=lo, w_max=hi,
                                        flags=wst.WST_FLAG_KAHAN, planes_per_chunk=min(8, work.n_w),
-                                       oversample=args.oversample, **kcfg), device=dev)
+                                       oversample=args.oversample, grid_n=grid_n, **kcfg), device=dev)
             if table is not None:
                 plan.set_kernel_table(table)
             plan.set_vis(d_u, d_v, d_ws, d_vis)
             plan.image(out=img)
             snapped = accuracy_block(torch, wst, work, plan.stats(), d_u, d_v, d_ws, d_vis, img, dev,
                                      args.dft_pixels, args.kernel, cfg.support, sigma,
-                                     None if table is None else tab_np, False, max(1, args.oversample), plan=plan)
+                                     None if table is None else tab_np, False, osf, plan=plan, n_img=img_n,
+                                     fov_img=img_fov)
             acc["w_snapped"] = {k2: snapped[k2] for k2 in (
                 "max_err_rel_peak", "central_max_err_rel_peak", "inner3q_max_err_rel_peak",
                 "inner3q_rms_err_rel_peak", "max_err_over_bound", "bound_rel_peak", "kernel_error_max")}
@@ -763,7 +776,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         job_s, sample, cores, osample, extrap, _ = time_oracle_sample(work, vis_np)
         cpu = {"value": round(n_vis / job_s / 1e6, 4), "unit": "Mvis/s", "cores": cores, "kind": "oracle",
                "sample": sample, "extrapolation": extrap}
-        if args.kernel == "gauss" and not args.snap_w and not args.wfold and args.oversample < 2:
+        if args.kernel == "gauss" and not args.snap_w and not args.wfold and args.oversample < 2 and not args.image_n:
             cpu["parity_vs_oracle"] = oracle_parity(torch, wst, dev, osample)
 
     clocks = clk.summary()
@@ -775,7 +788,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": work.n, "n_w": work.n_w,
                        "n_vis": n_vis, "batch": batch, "kernel": args.kernel, "support": cfg.support, "snap_w": args.snap_w,
                        "table_samples": None if table is None else int(tab_np.size),
-                       "wfold": args.wfold, "oversample": max(1, args.oversample),
+                       "wfold": args.wfold, "oversample": round(osf, 4), "image_n": img_n,
+                       "grid_n": grid_n or int(round(img_n * osf)),
                        "planes_per_chunk": args.chunk or planes,
                        "n_chunks": st["n_chunks"], "kept": st["n_kept"], "dropped": st["n_dropped"],
                        "rows_gridded": st["n_rows_gridded"],

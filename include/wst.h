@@ -86,7 +86,8 @@ enum {
 #define WST_NO_CORRECTION 0x1u /* omit the 1/(Ghat(nu_a) Ghat(nu_b)) grid correction */
 
 typedef struct wst_config {
-  int32_t n;                /* image side N, power of two, 64..16384                  */
+  int32_t n;                /* image side N: a power of two, 64..16384; with grid_n   */
+                            /* set, any even N with 64 <= N <= grid_n                  */
   double fov;               /* field of view in radians (> 0)                          */
   int32_t n_w;              /* w-planes per image, 1..4096                             */
   double w_min, w_max;      /* plane range (wavelengths); equal => min/max of the data */
@@ -100,6 +101,11 @@ typedef struct wst_config {
   int32_t oversample;       /* 0 or 1: grid = image (the paper's design); 2: a grid of  */
                             /* 2N cells of 1/(2 fov) wavelengths, the same pixels, the */
                             /* image the central N x N (2N <= 16384)                   */
+  int32_t grid_n;           /* 0: the grid side M follows from oversample; otherwise M  */
+                            /* itself, a power of two, N <= M <= 16384 (oversample 0 or */
+                            /* 1): M cells of N/(M fov) wavelengths, the image the      */
+                            /* central N x N of the M x M transform, oversampling       */
+                            /* factor M/N (1.25 for N = 3276, M = 4096)                 */
 } wst_config;
 
 typedef struct wst_stats {
@@ -216,7 +222,7 @@ wst_status wst_plan_set_vis_rows(wst_plan plan, int64_t n_vis, const double *uvw
 /*
  * Eq. 3: grid planes [plane_begin, plane_end) (global plane index image*N_w + k)
  * into grid_out, complex64 [(plane_end - plane_begin) x M x M], natural layout, M the
- * grid side (N, or 2N with oversample = 2).
+ * grid side (N; 2N with oversample = 2; grid_n when set).
  */
 wst_status wst_grid(wst_plan plan, int32_t plane_begin, int32_t plane_end, void *grid_out);
 
@@ -261,7 +267,7 @@ wst_status wst_image_range(wst_plan plan, int32_t plane_begin, int32_t plane_end
  * Adjoint of wst_image (degridding; the paper lists it as future work in its
  * conclusions): dvis_j = w_j sum_taps G G g_k[q,p], g_k the centred 2D transform
  * with the negative exponent of conj(screen_k) * C_a C_b * dimage.
- * WST_ERR_UNSUPPORTED with WST_FLAG_WFOLD.  With an oversampled grid (oversample = 2)
+ * WST_ERR_UNSUPPORTED with WST_FLAG_WFOLD.  With an oversampled grid (M > N)
  * the image enters the grid zero-padded around its central N x N, the adjoint of the
  * forward crop.  dimage: complex64 [batch x N x N]; dvis_out: complex64 [n_vis] in the
  * caller's order (0 for dropped and non-finite visibilities).

@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     OracleConfig,
     build,
     degrid,
+    degrid_on_grid,
     degrid_oversampled,
     dft_pixels,
     expand_rows,
@@ -20,12 +21,15 @@ from .oracle import (  # noqa: F401
     fold_w,
     gauss_legendre,
     grid,
+    grid_config,
     image,
+    image_on_grid,
     image_oversampled,
     image_pixels,
     kernel_eval,
     kernel_ft,
     kernel_grad,
+    kernel_grad_on_grid,
     kernel_grad_oversampled,
     locate,
     n_minus_one,

@@ -18,11 +18,14 @@ Every function follows a passage of arXiv:2301.06061:
 * ``kernel_ft``     -- Ghat(nu), the Fourier transform of the truncated kernel
 * ``fold_w``        -- the w-folding variant's Hermitian mirror of w < 0 visibilities
                        (not in the paper; applied to the inputs of the functions above)
-* ``image_oversampled`` -- the oversampled-grid variant (not in the paper): ``image``
-                       on a grid of 2N cells, cropped to the central N x N
-* ``degrid_oversampled``, ``kernel_grad_oversampled`` -- its adjoint and kernel gradient:
-                       the image zero-padded to the grid (the adjoint of the crop), then
-                       ``degrid`` / ``kernel_grad`` on the grid
+* ``image_on_grid`` -- the oversampled-grid variant (not in the paper): ``image``
+                       on a grid of M cells (a power of two, M >= N; ``grid_config``),
+                       cropped to the central N x N (N even, any size), oversampling
+                       factor M/N; ``image_oversampled`` is the case M = 2N
+* ``degrid_on_grid``, ``kernel_grad_on_grid`` (and the ``_oversampled`` M = 2N cases)
+                    -- its adjoint and kernel gradient: the image zero-padded to the
+                       grid (the adjoint of the crop), then ``degrid`` / ``kernel_grad``
+                       on the grid
 * ``expand_rows``   -- per-visibility (u, v, w) in wavelengths from per-row baseline
                        coordinates in metres and per-channel nu / c (the layout of
                        the LOFAR datasets of section 4; input expansion only)
@@ -33,10 +36,11 @@ screen; brute-force DFT within the analytic aliasing bound for the image;
 linearity, Hermitian symmetry and the single-visibility flat image; the
 dot-product identity for the adjoint; finite differences for the kernel
 gradient; exact integer placement rules for ``locate``; for ``fold_w``, the
-invariance of the real part of the direct transform; for ``image_oversampled``, the
-direct transform within the aliasing bound of the half-band frequencies; for
-``degrid_oversampled``, the dot-product identity with ``image_oversampled``; for
-``kernel_grad_oversampled``, central differences of ``image_oversampled``; for
+invariance of the real part of the direct transform; for ``image_on_grid``, the
+direct transform within the aliasing bound of the frequencies |nu| <= N/(2M) the image
+keeps (M = 2N, and M/N = 1.28 and 1.51 with N not a power of two); for
+``degrid_on_grid``, the dot-product identity with ``image_on_grid``; for
+``kernel_grad_on_grid``, central differences of ``image_on_grid``; for
 ``expand_rows``, exactly representable products, the (row, channel) order with a
 partial last row, and a product whose one rounding differs from rounding its factors
 first.
@@ -291,44 +295,72 @@ def image(cfg: OracleConfig, u, v, w, vis, weight=None, correct: bool = True) ->
     return out
 
 
-def image_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, weight=None,
-                      correct: bool = True) -> np.ndarray:
-    """The oversampled-grid variant (not in the paper): the image of ``cfg`` (N pixels of
-    fov/N) as the central N x N of the plain algorithm run on a grid of oversample * N
-    cells of 1/(oversample * fov) wavelengths -- the same pixels, a wider transform."""
-    n = cfg.n
-    big = OracleConfig(n * oversample, cfg.fov * oversample, cfg.n_w, cfg.w_min, cfg.w_max, cfg.support,
-                       cfg.kernel, cfg.kparam, cfg.ktable)
-    full = image(big, u, v, w, vis, weight, correct)
-    c = (n * oversample - n) // 2
-    return full[c:c + n, c:c + n].copy()
-
-
-def _big(cfg: OracleConfig, oversample: int) -> OracleConfig:
-    return OracleConfig(cfg.n * oversample, cfg.fov * oversample, cfg.n_w, cfg.w_min, cfg.w_max, cfg.support,
+def grid_config(cfg: OracleConfig, m: int) -> OracleConfig:
+    """The configuration of an m-cell grid (m a power of two, m >= n) with the pixels of
+    ``cfg``: cells of n/(m fov) wavelengths, i.e. a field of fov m / n computed as
+    (fov m) / n, one rounding (the order the library uses, so that placement decisions
+    agree bit for bit)."""
+    n = int(cfg.n)
+    if m < n or m & (m - 1):
+        raise ValueError("the grid side must be a power of two no smaller than the image")
+    return OracleConfig(m, cfg.fov * m / n, cfg.n_w, cfg.w_min, cfg.w_max, cfg.support,
                         cfg.kernel, cfg.kparam, cfg.ktable)
 
 
-def _zero_pad(dimage, n: int, oversample: int) -> np.ndarray:
-    """The N x N image in the centre of a zero (oversample N)^2 grid image: the adjoint of
-    the centre crop of ``image_oversampled``."""
-    big = np.zeros((n * oversample, n * oversample), np.complex128)
-    c = (n * oversample - n) // 2
+def _crop_offset(n: int, m: int) -> int:
+    if n % 2:
+        raise ValueError("an image cropped from a larger grid has an even side")
+    return (m - n) // 2
+
+
+def image_on_grid(cfg: OracleConfig, m: int, u, v, w, vis, weight=None, correct: bool = True) -> np.ndarray:
+    """The oversampled-grid variant (not in the paper): the image of ``cfg`` (n pixels of
+    fov/n, n even, any size) as the central n x n of the plain algorithm run on a grid of
+    m cells (``grid_config``): the same pixels, a wider transform, oversampling factor
+    m/n.  Grid pixel a + c, c = (m - n)/2, is image pixel a: both sit at
+    (a - n/2) fov/n."""
+    n = int(cfg.n)
+    c = _crop_offset(n, m)
+    full = image(grid_config(cfg, m), u, v, w, vis, weight, correct)
+    return full[c:c + n, c:c + n].copy()
+
+
+def image_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, weight=None,
+                      correct: bool = True) -> np.ndarray:
+    """``image_on_grid`` with m = oversample * n."""
+    return image_on_grid(cfg, oversample * int(cfg.n), u, v, w, vis, weight, correct)
+
+
+def _zero_pad(dimage, n: int, m: int) -> np.ndarray:
+    """The n x n image in the centre of a zero m x m grid image: the adjoint of the centre
+    crop of ``image_on_grid``."""
+    big = np.zeros((m, m), np.complex128)
+    c = _crop_offset(n, m)
     big[c:c + n, c:c + n] = np.asarray(dimage, np.complex128).reshape(n, n)
     return big
 
 
+def degrid_on_grid(cfg: OracleConfig, m: int, u, v, w, vis, dimage, weight=None, correct: bool = True) -> np.ndarray:
+    """Adjoint of ``image_on_grid``: the image is zero-padded to the m x m grid (the
+    adjoint of the crop) and degridded by ``degrid`` on that grid."""
+    return degrid(grid_config(cfg, m), u, v, w, vis, _zero_pad(dimage, int(cfg.n), m), weight, correct)
+
+
+def kernel_grad_on_grid(cfg: OracleConfig, m: int, u, v, w, vis, dimage, weight=None) -> np.ndarray:
+    """Gradient of Re<dimage, U> w.r.t. the kernel table, U the uncorrected
+    ``image_on_grid``: ``kernel_grad`` on the grid with the zero-padded dimage."""
+    return kernel_grad(grid_config(cfg, m), u, v, w, vis, _zero_pad(dimage, int(cfg.n), m), weight)
+
+
 def degrid_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, dimage, weight=None,
                        correct: bool = True) -> np.ndarray:
-    """Adjoint of ``image_oversampled``: the image is zero-padded to the (oversample N)^2
-    grid (the adjoint of the crop) and degridded by ``degrid`` on that grid."""
-    return degrid(_big(cfg, oversample), u, v, w, vis, _zero_pad(dimage, cfg.n, oversample), weight, correct)
+    """``degrid_on_grid`` with m = oversample * n."""
+    return degrid_on_grid(cfg, oversample * int(cfg.n), u, v, w, vis, dimage, weight, correct)
 
 
 def kernel_grad_oversampled(cfg: OracleConfig, oversample: int, u, v, w, vis, dimage, weight=None) -> np.ndarray:
-    """Gradient of Re<dimage, U> w.r.t. the kernel table, U the uncorrected
-    ``image_oversampled``: ``kernel_grad`` on the grid with the zero-padded dimage."""
-    return kernel_grad(_big(cfg, oversample), u, v, w, vis, _zero_pad(dimage, cfg.n, oversample), weight)
+    """``kernel_grad_on_grid`` with m = oversample * n."""
+    return kernel_grad_on_grid(cfg, oversample * int(cfg.n), u, v, w, vis, dimage, weight)
 
 
 def image_pixels(cfg: OracleConfig, u, v, w, vis, pa, pb, weight=None,

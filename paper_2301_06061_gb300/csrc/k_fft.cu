@@ -546,7 +546,9 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
+  // only the bands that hold image columns (from the band of column crop: the image's
+  // side need not be a multiple of the band, nor crop of its width)
+  const int col0 = (crop / kCB + (int)blockIdx.x) * kCB;
   const int kp = col0 + col;
   auto smi = [col](int i) { return i * C::PADW + col; };
   const bool kahan = flags & ACC_KAHAN;
@@ -629,7 +631,8 @@ k_cols_b_acc(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       for (int r = 0; r < RL; ++r) {
         const int e = b * RL + r;
         const int kq = c + B * out_index<LA, EPT, TPL, NST - 1>(jt, b, r);
-        if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
+        if (CROP && (kq < crop || kq >= crop + n_img || kp < crop || kp >= crop + n_img))
+          continue;  // a grid row or column outside the image
         const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
         flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
@@ -655,7 +658,9 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
+  // only the bands that hold image columns (from the band of column crop: the image's
+  // side need not be a multiple of the band, nor crop of its width)
+  const int col0 = (crop / kCB + (int)blockIdx.x) * kCB;
   const int kp = col0 + col;
   const bool kahan = flags & ACC_KAHAN;
   const size_t plane_elems = (size_t)n * n;
@@ -758,7 +763,8 @@ k_cols_b16(const float2 *__restrict__ planes, int p0, int p1, int n_w, Tw tw,
       for (int r = 0; r < R1; ++r) {
         const int e = b * R1 + r;
         const int kq = out_row(b, r);
-        if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
+        if (CROP && (kq < crop || kq >= crop + n_img || kp < crop || kp >= crop + n_img))
+          continue;  // a grid row or column outside the image
         const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
         flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), s[e], cc[e], first_any, last_any, flags, f);
       }
@@ -811,7 +817,9 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
-  const int col0 = crop + blockIdx.x * kCB;  // only the image's columns of the grid
+  // only the bands that hold image columns (from the band of column crop: the image's
+  // side need not be a multiple of the band, nor crop of its width)
+  const int col0 = (crop / kCB + (int)blockIdx.x) * kCB;
   const int kp = col0 + col;
   const bool kahan = flags & ACC_KAHAN;
   const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(&s_mbar[0]);
@@ -943,7 +951,8 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const int kq = out_row(e);
-      if (CROP && (kq < crop || kq >= crop + n_img)) continue;  // a grid row outside the image
+      if (CROP && (kq < crop || kq >= crop + n_img || kp < crop || kp >= crop + n_img))
+          continue;  // a grid row or column outside the image
       const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
       flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), S[e], Cc[e], first_any, last_any, flags, f);
     }
@@ -1200,7 +1209,8 @@ static bool plane_tile_map(CUtensorMap *m, const float2 *planes, int n, int npla
 template <int LA, bool FP64S, bool CROP>
 static void launch_cols_b_variant(wst_plan_s *p, const float2 *planes, int p0, int p1, float2 *image,
                                   float2 *comp, int flags) {
-  dim3 grd(p->n_img / kCB, p->n / LA);  // the image's column bands of the grid, every row block
+  // the grid's column bands that hold image columns, every row block
+  dim3 grd((p->crop + p->n_img + kCB - 1) / kCB - p->crop / kCB, p->n / LA);
   if constexpr (LA == 64 || LA == 128) {
     CUtensorMap map;
     if (plane_tile_map(&map, planes, p->n, p1 - p0, LA))

@@ -151,15 +151,24 @@ wst_status wst_plan_create(const wst_config *cfg, void *cuda_stream, wst_plan *o
   *out = nullptr;
   if (!cfg) return WST_ERR_INVALID_ARG;
   if (cfg->oversample < 0 || cfg->oversample > 2) return WST_ERR_UNSUPPORTED;
-  const int os = cfg->oversample == 2 ? 2 : 1;
-  // the plan works on the grid: os N cells of 1/(os fov) (the same pixel size), and
-  // images are the central N x N of the grid's transform
+  if (cfg->grid_n < 0 || (cfg->grid_n > 0 && cfg->oversample == 2)) return WST_ERR_INVALID_ARG;
+  // the plan works on the grid: M cells of N/(M fov) wavelengths (the image's pixel
+  // size), and images are the central N x N of the grid's transform
+  int m = 0;
+  if (cfg->grid_n > 0) {
+    if (!is_pow2(cfg->grid_n) || cfg->grid_n < 64 || cfg->grid_n > 16384) return WST_ERR_UNSUPPORTED;
+    if (cfg->n < 64 || cfg->n > cfg->grid_n || (cfg->n & 1)) return WST_ERR_UNSUPPORTED;
+    m = cfg->grid_n;
+  } else {
+    if (!is_pow2(cfg->n) || cfg->n < 64) return WST_ERR_UNSUPPORTED;
+    m = cfg->n * (cfg->oversample == 2 ? 2 : 1);
+    if (m > 16384) return WST_ERR_UNSUPPORTED;
+  }
   wst_config c = *cfg;
-  if (!is_pow2(cfg->n) || cfg->n < 64) return WST_ERR_UNSUPPORTED;
-  c.n = cfg->n * os;
-  c.fov = cfg->fov * os;
-  c.oversample = os;
-  if (c.n > 16384) return WST_ERR_UNSUPPORTED;
+  c.n = m;
+  c.fov = cfg->fov * (double)m / (double)cfg->n;  // (fov M) / N: one rounding
+  c.oversample = m == cfg->n ? 1 : 2;
+  c.grid_n = m;
   if (!(c.fov > 0.0) || !isfinite(c.fov)) return WST_ERR_INVALID_ARG;
   if (c.n_w < 1 || c.n_w > 4096) return WST_ERR_INVALID_ARG;
   if (!isfinite(c.w_min) || !isfinite(c.w_max) || c.w_min > c.w_max) return WST_ERR_INVALID_ARG;

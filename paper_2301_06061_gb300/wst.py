@@ -56,6 +56,7 @@ class wst_config(ctypes.Structure):
         ("planes_per_chunk", ctypes.c_int32),
         ("batch", ctypes.c_int32),
         ("oversample", ctypes.c_int32),
+        ("grid_n", ctypes.c_int32),
     ]
 
 
@@ -331,11 +332,12 @@ class Config:
     planes_per_chunk: int = 0
     batch: int = 1
     oversample: int = 0
+    grid_n: int = 0  # grid side M (a power of two >= n); 0: n, or 2n with oversample = 2
 
     def c(self) -> wst_config:
         return wst_config(self.n, self.fov, self.n_w, self.w_min, self.w_max, self.support, self.kernel,
                           self.kparam, self.ktable_len, self.flags, self.planes_per_chunk, self.batch,
-                          self.oversample)
+                          self.oversample, self.grid_n)
 
 
 DEFAULT_SIGMA = {7: 0.875, 8: 0.925}

@@ -113,6 +113,10 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     (dict(w_min=10.0, w_max=-10.0), 1), (dict(w_max=float("inf")), 1), (dict(support=1), 5),
     (dict(support=17), 5), (dict(kernel=7), 1), (dict(kparam=-1.0), 1), (dict(kernel=2, ktable_len=1), 1),
     (dict(flags=0x100), 1), (dict(batch=0), 1), (dict(planes_per_chunk=-1), 1),
+    # an explicit grid side: a power of two in [N, 16384], N even and >= 64, not with oversample = 2
+    (dict(n=200, grid_n=0), 5), (dict(n=200, grid_n=200), 5), (dict(n=200, grid_n=128), 5),
+    (dict(n=201, grid_n=256), 5), (dict(n=48, grid_n=64), 5), (dict(n=10000, grid_n=32768), 5),
+    (dict(grid_n=-256), 1), (dict(grid_n=512, oversample=2), 1),
 ])
 def test_plan_create_rejects_invalid_configs_before_touching_the_device(lib, change, status):
     """Configuration errors come back as WST_ERR_INVALID_ARG (1) or WST_ERR_UNSUPPORTED
@@ -121,7 +125,7 @@ def test_plan_create_rejects_invalid_configs_before_touching_the_device(lib, cha
     from paper_2301_06061_gb300 import wst
 
     fields = dict(n=256, fov=0.1, n_w=4, w_min=-200.0, w_max=200.0, support=7, kernel=0, kparam=0.875,
-                  ktable_len=0, flags=1, planes_per_chunk=0, batch=1, oversample=0)
+                  ktable_len=0, flags=1, planes_per_chunk=0, batch=1, oversample=0, grid_n=0)
     fields.update(change)
     cfg = wst.wst_config(*[fields[name] for name, _ in wst.wst_config._fields_])
     h = ctypes.c_void_p(12345)

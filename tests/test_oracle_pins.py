@@ -640,6 +640,85 @@ def test_oversampled_kernel_grad_finite_differences():
         assert abs(fd - g[i]) < 1e-8 * max(1.0, np.abs(g).max())
 
 
+@pytest.mark.parametrize("N,M", [(100, 128), (170, 256), (204, 256)])
+def test_image_on_a_grid_of_any_oversampling_within_aliasing_bound(N, M):
+    """Oversampling factor M/N between 1 and 2 (1.28, 1.51, 1.25), N not a power of two:
+    image pixel a is grid pixel a + (M - N)/2, at frequency nu = (a - N/2)/M, |nu| <=
+    N/(2M); with w snapped, the direct transform lies within sum|V| (e_a + e_b + e_a e_b)
+    of the image over the WHOLE image, e taken at those frequencies."""
+    fov, n_vis = 0.1, 300
+    rng = np.random.default_rng(9)
+    u, v, w = synth.disk_uvw(n_vis, 0.45 * N / fov, 200.0, rng)
+    cfg = OracleConfig(N, fov, 5, -200.0, 200.0, 7, "gauss", 0.875)
+    k, _, _, st = oracle.locate(cfg, u, v, w, np.ones(n_vis, np.complex64))
+    assert np.all(st == 0)
+    w = np.array([oracle.plane_centre(cfg, int(kk)) for kk in k], np.float32)
+    vis = synth.random_visibilities(n_vis, rng)
+    img = oracle.image_on_grid(cfg, M, u, v, w, vis)
+    assert img.shape == (N, N)
+    a, b = np.meshgrid(np.arange(N), np.arange(N))
+    d = oracle.dft_pixels(u, v, w, vis, N, fov, a.ravel(), b.ravel()).reshape(N, N)
+    nu = (np.arange(N) - N // 2) / M
+    e = gauss_alias(nu, cfg.kparam, cfg.support)
+    bound = np.abs(vis).astype(np.float64).sum() * (e[None, :] + e[:, None] + e[None, :] * e[:, None])
+    assert np.all(np.abs(img - d) <= bound * (1 + 1e-9) + 1e-9)
+    # a wider grid for the same image keeps lower frequencies only: a smaller error
+    wide = oracle.image_on_grid(cfg, 4 * M, u, v, w, vis)
+    assert np.abs(wide - d).max() * 5 < np.abs(img - d).max()
+
+
+def test_grid_config_is_the_plain_config_scaled_and_checks_its_inputs():
+    cfg = OracleConfig(100, 0.1, 3, -1.0, 1.0)
+    g = oracle.grid_config(cfg, 128)
+    assert g.n == 128 and g.fov == 0.1 * 128 / 100 and g.n_w == 3
+    assert oracle.grid_config(OracleConfig(64, 0.1, 3, -1.0, 1.0), 128).fov == 0.2  # exact
+    with pytest.raises(ValueError):
+        oracle.grid_config(cfg, 96)  # not a power of two
+    with pytest.raises(ValueError):
+        oracle.grid_config(cfg, 64)  # smaller than the image
+    u = v = w = np.zeros(1, np.float32)
+    with pytest.raises(ValueError):
+        oracle.image_on_grid(OracleConfig(101, 0.1, 1, -1.0, 1.0), 128, u, v, w, np.ones(1, np.complex64))
+
+
+def test_degrid_on_grid_is_adjoint_dot_product():
+    """<y, A x> = <A^H y, x> for the image cropped from a grid of 1.28 N cells (N = 50)."""
+    N, M, fov = 50, 64, 0.1
+    rng = np.random.default_rng(25)
+    u, v, w = synth.disk_uvw(150, 0.45 * N / fov, 200.0, rng)
+    wt = rng.uniform(0.5, 2.0, 150).astype(np.float32)
+    x = synth.random_visibilities(150, rng)
+    cfg = OracleConfig(N, fov, 3, -200.0, 200.0, 7)
+    y = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    for corr in (True, False):
+        Ax = oracle.image_on_grid(cfg, M, u, v, w, x, wt, correct=corr)
+        Ahy = oracle.degrid_on_grid(cfg, M, u, v, w, x, y, wt, correct=corr)
+        assert abs(np.vdot(y, Ax) - np.vdot(Ahy, x.astype(complex))) < 1e-11 * abs(np.vdot(y, Ax))
+
+
+def test_kernel_grad_on_grid_finite_differences():
+    N, M, fov, W = 50, 64, 0.1, 8
+    L = W * 4 + 1
+    rng = np.random.default_rng(26)
+    u, v, w = synth.disk_uvw(50, 0.45 * N / fov, 200.0, rng)
+    vis = synth.random_visibilities(50, rng)
+    tab = np.exp(-np.linspace(-W / 2, W / 2, L) ** 2 / (2 * 0.925**2))
+    cfg = OracleConfig(N, fov, 3, -200.0, 200.0, W, "table", 0.0, tab)
+    dU = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    g = oracle.kernel_grad_on_grid(cfg, M, u, v, w, vis, dU)
+
+    def loss(t):
+        c = OracleConfig(N, fov, 3, -200.0, 200.0, W, "table", 0.0, t)
+        return np.real(np.vdot(dU, oracle.image_on_grid(c, M, u, v, w, vis, correct=False)))
+
+    h = 1e-3
+    for i in (0, 5, L // 2, L - 3, L - 1):
+        tp, tm = tab.copy(), tab.copy()
+        tp[i] += h
+        tm[i] -= h
+        assert abs((loss(tp) - loss(tm)) / (2 * h) - g[i]) < 1e-8 * max(1.0, np.abs(g).max())
+
+
 # ------------------------------------------------------------------------------------------
 # inputs by row and channel (the layout of the LOFAR datasets of section 4)
 # ------------------------------------------------------------------------------------------
