@@ -130,13 +130,65 @@ __device__ __forceinline__ void cp_async16_rg(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+// The previous row's transformed values, written out while this row is gridded: four of
+// a thread's outputs per record it grids, the rest when its gridding ends, so that a
+// row's 128 KB leave the SM spread over the next row's gridding instead of in one burst
+// at the end of its transform.
+template <int N>
+struct PendingRow {
+  static constexpr int EPT = RowCfg<N>::EPT, TPR = RowCfg<N>::TPR, CH = 4, NCH = EPT / CH;
+  static constexpr int NST = num_stages(N, EPT), RL = stage_radix(N, EPT, NST - 1);
+  float2 v[EPT];
+  float2 *orow;
+  int next;  // next group of CH outputs to write; NCH: nothing pending
+  // one group, chosen by a chain of branches whose stores are separate asm statements
+  // (a merged store would index v at run time and move it out of registers)
+  template <int C>
+  __device__ __forceinline__ void write_group(int jt) {
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int e = C * CH + k;  // output e = b RL + r of the last stage
+      float2 *a = orow + out_index<N, EPT, TPR, NST - 1>(jt, e / RL, e % RL);
+      asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(v[e].x), "f"(v[e].y) : "memory");
+    }
+  }
+  template <int C = 0>
+  __device__ __forceinline__ void write_chain(int jt) {
+    if constexpr (C < NCH) {
+      if (next == C) write_group<C>(jt);
+      else write_chain<C + 1>(jt);
+    }
+  }
+  __device__ __forceinline__ void write_one(int jt) {
+    if (next >= NCH) return;
+    write_chain(jt);
+    ++next;
+  }
+  __device__ __forceinline__ void write_all(int jt) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+      if (c >= next) {
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          const int e = c * CH + k;
+          __stcs(&orow[out_index<N, EPT, TPR, NST - 1>(jt, e / RL, e % RL)], v[e]);
+        }
+      }
+    next = NCH;
+  }
+};
+struct NoPending {
+  __device__ __forceinline__ void write_one(int) {}
+  __device__ __forceinline__ void write_all(int) {}
+};
+
 // With FIXED, qscale = 1/delta and gmax the largest |kernel value|: a record whose scaled
 // value times gmax comes within 0.2% of 2^31 (a margin for the rounding of the taps)
 // could saturate a conversion, and sends the row to float atomics like a wrapped sum.
-template <int N, int WT, bool FIXED>
+template <int N, int WT, bool FIXED, class PEND>
 __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__restrict__ rec,
                                         const uint32_t *bnd, int d_lo, const KernelParams &kp, int jt,
-                                        float qscale, float gmax, RecHead *stg, int stg_stride) {
+                                        float qscale, float gmax, RecHead *stg, int stg_stride, PEND &pd) {
   constexpr int TPR = RowCfg<N>::TPR;
   int ovf = 0;
   const uint32_t s_end = bnd[d_lo + 1];
@@ -172,6 +224,7 @@ __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__
       if (FIXED && fmaxf(fabsf(vre), fabsf(vim)) * gmax >= 0x1.ffp30f) ovf = -1;
 #pragma unroll
       for (int a = 0; a < WT; ++a) add_tap<FIXED>(sre, sim, i0 + a, vre * g[a], vim * g[a], ovf);
+      pd.write_one(jt);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else {
@@ -190,19 +243,22 @@ __device__ __forceinline__ int grid_row(float *sre, float *sim, const Record *__
         const float g = kernel_eval(kp, (float)a - kp.half + gx);
         add_tap<FIXED>(sre, sim, i0 + a, vre * g, vim * g, ovf);
       }
+      pd.write_one(jt);
     }
   }
   return ovf;
 }
 
-// One non-empty row q of a plane: accumulate, transform (FFT) and write it.  Every
-// thread of the row group calls it; it ends with the row buffer free again.
-template <int N, bool FFT, int WT>
+// One non-empty row q of a plane: accumulate, transform (FFT) and write it (with a
+// PendingRow, during the next row's gridding: pd holds the row before this one on entry
+// and this row on return).  Every thread of the row group calls it; it ends with the row
+// buffer free again.
+template <int N, bool FFT, int WT, class PEND>
 __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const Record *__restrict__ rec,
                                              const uint32_t *__restrict__ off, int64_t b0, int q, bool nonempty,
                                              const KernelParams &kp, float2 *__restrict__ orow,
                                              const float2 *twt, int jt, const float2 *__restrict__ rowbound,
-                                             float gmax, RecHead *stg, int stg_stride) {
+                                             float gmax, RecHead *stg, int stg_stride, PEND &pd) {
   using C = RowCfg<N>;
   constexpr int EPT = C::EPT, TPR = C::TPR;
   constexpr int NST = num_stages(N, EPT);
@@ -234,8 +290,9 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   bool fx = fixed;
   int ovf = 0;
   if (nonempty) {
-    if (fixed) ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit), gmax, stg, stg_stride);
-    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride);
+    if (fixed)
+      ovf = grid_row<N, WT, true>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f / (bound * unit), gmax, stg, stg_stride, pd);
+    else grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride, pd);
   }
   bool redo = false;  // a tap or a partial sum left the int32 range: accumulate in float
   if constexpr (kFixedRows<N>) redo = __syncthreads_or(ovf < 0);
@@ -243,10 +300,11 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   if (redo) {
     zero_row<N>(srow, jt);
     __syncthreads();
-    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride);
+    if (nonempty) grid_row<N, WT, false>(sre, sim, rec, bnd, d_lo, kp, jt, 1.0f, gmax, stg, stg_stride, pd);
     fx = false;
     __syncthreads();
   }
+  pd.write_all(jt);  // the previous row is out before this one's transform takes its place
   const float delta = fx ? bound * unit : 1.0f;
   const int *ire = reinterpret_cast<const int *>(sre), *iim = reinterpret_cast<const int *>(sim);
   if constexpr (FFT) {
@@ -275,7 +333,14 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
     stage_compute_f<N, EPT, TPR, 0, 1>(v, jt, twp);
     middle_stages_f<N, EPT, TPR, 1, 1>(v, jt, srow, smi, twp);
     stage_compute_f<N, EPT, TPR, NST - 1, 1>(v, jt, twp);
-    if (orow && nonempty) {
+    if constexpr (std::is_same_v<PEND, PendingRow<N>>) {
+      // kept for the next row's gridding (assigned on every path, so that the old values
+      // are dead after their last write)
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) pd.v[e] = v[e];
+      pd.orow = orow;
+      pd.next = (orow && nonempty) ? 0 : PEND::NCH;
+    } else if (orow && nonempty) {
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
@@ -340,6 +405,12 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
     // CTA then grids and transforms only those; the next batch is fetched meanwhile
     __shared__ int s_list[kRowBatch], s_cnt;
     unsigned long long next = 0;
+    // the transforming path writes each row during the next row's gridding
+    std::conditional_t<FFT, PendingRow<N>, NoPending> pd;
+    if constexpr (FFT) {
+      pd.next = PendingRow<N>::NCH;
+      pd.orow = nullptr;
+    }
     if (threadIdx.x == 0) next = atomicAdd(counter, (unsigned long long)kRowBatch);
     while (true) {
       if (threadIdx.x == 0) {
@@ -372,9 +443,10 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
         const long long item = base + (e >> 1);
         const int pl = (int)(item / N), q = (int)(item % N);
         grid_one_row<N, FFT, WT>(srow, s_bnd[0], rec, off, (int64_t)(p0 + pl) * N, q, e & 1, kp,
-                                 out + ((int64_t)pl * N + q) * N, twt, jt, rowbound, gmax, stg, stg_stride);
+                                 out + ((int64_t)pl * N + q) * N, twt, jt, rowbound, gmax, stg, stg_stride, pd);
       }
     }
+    pd.write_all(jt);  // the CTA's last row
   } else {
     while (true) {
       if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)RPC);
@@ -390,8 +462,9 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       if (valid && jt == 0) occ[item] = empty ? 0 : 1;
       if (rows_done && valid && jt == 0 && !empty) atomicAdd(rows_done, 1ull);
       float2 *orow = valid && (!FFT || !empty) ? out + ((int64_t)pl * N + q) * N : nullptr;
+      NoPending none;
       grid_one_row<N, FFT, WT>(srow, s_bnd[rl], rec, off, (int64_t)(p0 + pl) * N, q, !empty, kp, orow, twt, jt,
-                               rowbound, gmax, stg, stg_stride);
+                               rowbound, gmax, stg, stg_stride, none);
     }
   }
 }
