@@ -76,10 +76,11 @@ def parse():
                     help="2: grid of 2N cells, the central N x N kept (images up to 8192^2)")
     ap.add_argument("--wfold", action="store_true",
                     help="mirror w < 0 visibilities (WST_FLAG_WFOLD): half the w range; the real part is the image")
-    ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8", "es8", "kb8"], default="gauss",
+    ap.add_argument("--kernel", choices=["gauss", "learned", "gauss8", "es8", "kb8", "pswf8"], default="gauss",
                     help="gauss: W=7 Gaussian (the paper's); W=8 kernels: gauss8 Gaussian (sigma 0.925), es8 "
                          "exponential of semicircle (beta 2.3 W), kb8 Kaiser-Bessel table (beta of Beatty et "
-                         "al. for the grid's oversampling), learned the trained table "
+                         "al. for the grid's oversampling), pswf8 prolate spheroidal table (c = pi W (1 - "
+                         "1/(2 alpha))), learned the trained table "
                          "(paper_2301_06061_gb300/data/learned_kernel_w8.npz)")
     return ap.parse_args()
 
@@ -141,7 +142,7 @@ def random_values(work, rank: int):
 # ------------------------------------------------------------------------------------------
 
 def kernel_function(kernel: str, support: int, sigma: float, table):
-    """(G, quadrature panels) of a kernel: a tabulated one (learned, kb8) interpolated
+    """(G, quadrature panels) of a kernel: a tabulated one (learned, kb8, pswf8) interpolated
     linearly as the library does, es8's exponential of semicircle (sigma holds beta), or
     the Gaussian."""
     half = 0.5 * support
@@ -572,11 +573,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     elif args.kernel == "es8":
         kcfg = dict(support=8, kernel=wst.WST_KERNEL_ES, kparam=2.3 * 8)
     else:
-        if args.kernel == "kb8":
+        if args.kernel in ("kb8", "pswf8"):
             from paper_2301_06061_gb300 import kernels
 
             alpha = work.n / args.image_n if args.image_n else float(max(1, args.oversample))
-            tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, alpha), args.table_per_cell)
+            if args.kernel == "kb8":
+                tab_np = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, alpha), args.table_per_cell)
+            else:
+                tab_np = kernels.pswf_table(8, kernels.pswf_c(8, alpha), args.table_per_cell)
         else:
             from paper_2301_06061_gb300 import learned
 
