@@ -650,37 +650,52 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dom = max(stages, key=stages.get)
     per_launch_ms = stages[dom] / (args.steps * launches_per_stage[dom])
     planes = batch * work.n_w
-    bytes_launch = stage_bytes(dom, img_n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf)
     peak, peak_src = load_peaks()
-    achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     kernel_names = {"sort": "k_keys+k_scan+k_scatter+k_row_bounds", "grid": "k_grid_rows (gridding + row FFT)",
                     "rows": "k_rows", "cols_a": "k_cols_a16 (column stage A)",
                     "cols_b": "k_cols_b_tma (column stage B + phase screen + compensated plane sum)"}
-    # the bytes this design must move in the launch: the occupied rows the gridder writes
-    # and column stage A reads (rows no visibility reaches are known zero), the records,
-    # the planes and the image -- below the nominal bytes above wherever rows are empty
+    # algorithmic bytes of a launch: what this design must move -- the occupied rows the
+    # gridder writes and column stage A reads (rows no visibility reaches are known zero
+    # and never touched), the records, the planes and the image.  The nominal bytes
+    # (every row of every plane written and read, as a gridder without the occupancy
+    # would) are reported beside them.
     ones = {k: 1.0 for k in ("grid_read", "grid_write", "cols_a_read", "cols_a_write", "cols_b_read", "cols_b_write")}
-    needed = launch_traffic(dom, img_n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
-                            st["n_kept"] / st["n_chunks"], batch, osf, ratios=ones)
-    if needed is None:
-        needed = bytes_launch
+
+    def needed_bytes(stage):
+        b = launch_traffic(stage, img_n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
+                           st["n_kept"] / st["n_chunks"], batch, osf, ratios=ones)
+        return stage_bytes(stage, img_n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf) if b is None else b
+
+    def frac(nbytes, ms):
+        return round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)
+
+    bytes_launch = needed_bytes(dom)
+    nominal = stage_bytes(dom, img_n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf)
+    achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": launch_traffic(dom, img_n, planes / st["n_chunks"], st["n_rows_gridded"] / st["n_chunks"],
                                           st["n_kept"] / st["n_chunks"], batch, osf),
                 "traffic_source": "small-case ncu ratios (profiles/traffic_16384_small.md) times this launch's "
                                   "design bytes (n_rows_gridded occupied rows, records, planes, image)",
-                "bytes_per_launch": bytes_launch, "ms_per_launch": round(per_launch_ms, 4),
-                "needed_bytes_per_launch": needed,
-                "needed_frac": round(needed / (per_launch_ms * 1e-3) / 1e9 / peak, 4),
+                "bytes_per_launch": bytes_launch, "bytes": "occupied rows, records, planes, image (this design)",
+                "ms_per_launch": round(per_launch_ms, 4),
+                "nominal_bytes_per_launch": nominal, "nominal_frac": frac(nominal, per_launch_ms),
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stages.items()},
-                "stage_frac_of_hbm": {k: round(stage_bytes(k, img_n, planes, st["n_chunks"], batch, st["n_kept"],
-                                                           n_vis, osf) * launches_per_stage[k] /
-                                               (v / args.steps * 1e-3) / 1e9 / peak, 4)
-                                      for k, v in stages.items() if v > 0}}
+                "stage_frac_of_hbm": {k: frac(needed_bytes(k) * launches_per_stage[k], v / args.steps)
+                                      for k, v in stages.items() if v > 0},
+                "stage_frac_of_hbm_nominal": {
+                    k: frac(stage_bytes(k, img_n, planes, st["n_chunks"], batch, st["n_kept"], n_vis, osf) *
+                            launches_per_stage[k], v / args.steps) for k, v in stages.items() if v > 0}}
     roofline["step"] = step_roofline({k: v / args.steps for k, v in stages.items()}, img_n, planes,
                                      st["n_chunks"], batch, st["n_kept"], n_vis, osf, ms_step, peak)
+    # the step on this design's bytes (the nominal sum above counts every row of every plane)
+    step_needed = sum(needed_bytes(k) * launches_per_stage[k] for k, v in stages.items() if v > 0)
+    roofline["step"].update({"nominal_bytes": roofline["step"].pop("bytes"),
+                             "nominal_frac": roofline["step"].pop("frac"), "bytes": step_needed,
+                             "achieved": round(step_needed / (ms_step * 1e-3) / 1e9, 1),
+                             "frac": frac(step_needed, ms_step)})
 
     cufft = None
     if batch == 1 and not args.no_cufft:
