@@ -96,9 +96,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
 }
 
 // Wait for the phase with a time limit; a zero limit expires at once without looking
-// (the plan's failure-path test setting, wst_plan_set_wait_limit).
+// (the plan's failure-path test setting, wst_plan_set_wait_limit).  The clock is read
+// only once the first look finds the phase incomplete (the limit counts from there).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, unsigned long long limit_ns) {
   if (limit_ns == 0) return false;
+  if (mbar_try_wait(mbar, phase)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(mbar, phase)) {
     if (global_ns() - t0 > limit_ns) return false;

@@ -354,6 +354,30 @@ static cudaError_t scan_exclusive(uint32_t *data, int64_t n, uint32_t *tmp, cuda
 // the column bins its W taps reach (one or two) of its row bucket.
 constexpr int kScatterIlp = 4;
 
+// x added to bin[id] for every valid lane, with one global atomic per run of adjacent
+// lanes that share the bin (consecutive channels of one baseline often do): a segmented
+// inclusive scan over the warp leaves each run's sum in its last lane.  Every lane of the
+// warp calls it; invalid lanes take ids no bin has, so they start runs of their own.
+__device__ __forceinline__ void add_bin_runs(float *__restrict__ bin, uint64_t id, float x, bool valid) {
+  constexpr unsigned kFull = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  if (!valid) {
+    id = ~0ull - (uint64_t)lane;
+    x = 0.0f;
+  }
+  const uint64_t prev = __shfl_up_sync(kFull, id, 1), next = __shfl_down_sync(kFull, id, 1);
+  const bool tail = lane == 31 || next != id;
+  int start = (lane == 0 || prev != id) ? lane : 0;  // the run's first lane, by a max-scan
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) start = max(start, __shfl_up_sync(kFull, start, o));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, x, o);
+    if (lane - o >= start) x += y;
+  }
+  if (valid && tail) atomicAdd(bin + id, x);
+}
+
 __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restrict__ weight,
                           const uint4 *__restrict__ keyinfo, uint32_t *__restrict__ cursor, int64_t n_vis,
                           Record *__restrict__ records, float *__restrict__ binmag, int nb, int W,
@@ -397,18 +421,22 @@ __global__ void k_scatter(const float2 *__restrict__ vis, const float *__restric
     for (int h = 0; h < kScatterIlp; ++h) {
       const bool kept = ki[h].x != kDropKey;
       const uint32_t b = __shfl_sync(0xFFFFFFFFu, base[h], kept ? __ffs(peers[h]) - 1 : lane);
+      float vre = 0.0f, vim = 0.0f;
+      if (kept) {
+        vre = val[h].x * wt[h];
+        vim = (ki[h].y ? -val[h].y : val[h].y) * wt[h];  // mirrored: conj
+      }
+      if (binmag) {  // the whole warp: the first bin by runs, the second (rare) directly
+        const float mag = fmaxf(fabsf(vre), fabsf(vim));
+        const int i0 = (int)(ki[h].z >> 18);
+        const int bl = min(i0 >> kBinShift, nb - 1), bh = min((i0 + W - 1) >> kBinShift, nb - 1);
+        const uint64_t row0 = (uint64_t)(ki[h].x / kColBlocks) * (uint64_t)nb;
+        add_bin_runs(binmag, row0 + (uint64_t)bl, mag, kept);
+        if (kept && bh != bl) atomicAdd(binmag + row0 + bh, mag);
+      }
       if (!kept) continue;
       const uint32_t pos = b + __popc(peers[h] & ((1u << lane) - 1u));
       uint4 *dst = reinterpret_cast<uint4 *>(records + pos);
-      const float vre = val[h].x * wt[h], vim = (ki[h].y ? -val[h].y : val[h].y) * wt[h];  // mirrored: conj
-      const float mag = fmaxf(fabsf(vre), fabsf(vim));
-      if (binmag) {
-        const int i0 = (int)(ki[h].z >> 18);
-        const int bl = min(i0 >> kBinShift, nb - 1), bh = min((i0 + W - 1) >> kBinShift, nb - 1);
-        float *bins = binmag + (size_t)(ki[h].x / kColBlocks) * nb;
-        atomicAdd(bins + bl, mag);
-        if (bh != bl) atomicAdd(bins + bh, mag);
-      }
       dst[0] = make_uint4(ki[h].z, ki[h].w, __float_as_uint(vre), __float_as_uint(vim));
       dst[1] = make_uint4((uint32_t)(w0 + h * stride + lane), __float_as_uint(wt[h]), 0u, 0u);
     }

@@ -1,8 +1,9 @@
 """GPU parity for the configurations the benchmark reports numbers for, at their sizes.
 
-* W = 8 kernels (Gaussian sigma = 0.925 and the trained table) on the fixed-point rows
-  of images of 8192^2 and up: the full image at 8192^2 against ``oracle.image``, and
-  16384^2 at sampled pixels against ``oracle.image_pixels``;
+* W = 8 kernels (Gaussian sigma = 0.925, the trained table and the Kaiser-Bessel and
+  prolate spheroidal tables) on the fixed-point rows of images of 8192^2 and up: the
+  full image at 8192^2 against ``oracle.image``, and 16384^2 at sampled pixels against
+  ``oracle.image_pixels``;
 * the staged row FFT of a 16384-point grid (``wst_fft_correct``, the TMA-prefetched
   row kernel);
 * the batched workload at its real shape (64 images of 2048^2, 16 planes, 37.7M
@@ -20,7 +21,7 @@ import pytest
 
 import oracle
 from oracle import OracleConfig
-from paper_2301_06061_gb300 import synth
+from paper_2301_06061_gb300 import kernels, synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,10 +74,18 @@ def learned_table():
 
 
 def w8_kernel(wst, name):
-    """(wst.Config kwargs, oracle kernel args, device table or None) of a W = 8 kernel."""
+    """(wst.Config kwargs, oracle kernel args, device table or None) of a W = 8 kernel:
+    the Gaussian, the trained table, or the Kaiser-Bessel / prolate spheroidal window
+    tabulated for a grid the size of the image (oversampling 1)."""
     if name == "gauss8":
         return dict(support=8, kparam=0.925), ("gauss", 0.925, None), None
-    tab = learned_table().astype(np.float32)
+    if name == "kb8":
+        tab = kernels.kaiser_bessel_table(8, kernels.kaiser_bessel_beta(8, 1.0))
+    elif name == "pswf8":
+        tab = kernels.pswf_table(8, kernels.pswf_c(8, 1.0))
+    else:
+        tab = learned_table()
+    tab = tab.astype(np.float32)
     return (dict(support=8, kernel=wst.WST_KERNEL_TABLE, kparam=0.0, ktable_len=int(tab.size)),
             ("table", 0.0, tab.astype(np.float64)), dev(tab))
 
@@ -102,7 +111,7 @@ def dense_tracks(n_vis, seed):
 # W = 8 on fixed-point rows
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("kernel", ["gauss8", "learned"])
+@pytest.mark.parametrize("kernel", ["gauss8", "learned", "kb8", "pswf8"])
 def test_w8_fixed_point_rows_full_image_8192(wst, kernel):
     """The array workload's tracks (60 stations, 16 channels, 4.08M visibilities,
     core-dense) on an 8192^2 grid of FoV 0.2 (every row in the fixed-point path), 4
@@ -128,7 +137,7 @@ def test_w8_fixed_point_rows_full_image_8192(wst, kernel):
     assert_image_parity(img_c, ref_c, ocfg)
 
 
-@pytest.mark.parametrize("kernel", ["gauss8", "learned"])
+@pytest.mark.parametrize("kernel", ["gauss8", "learned", "kb8", "pswf8"])
 def test_w8_kernels_16384_sampled(wst, kernel):
     """16384^2, FoV 0.5 (the benchmark's geometry and fixed-point rows), 4 planes in 2
     chunks, 1.5M core-dense visibilities; 264 pixels against the oracle's pixel-wise
