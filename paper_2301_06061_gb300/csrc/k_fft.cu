@@ -816,6 +816,10 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
   constexpr int NTW = total_tw_count<LA, EPT>();
   __shared__ float2 s_tw1[NTW][TPL];
   __shared__ __align__(8) unsigned long long s_mbar[kColsBRing];
+  // l^2 (float-float) of the tile's LA grid rows c + B m and of its kCB columns, read
+  // once: every screen evaluation of the tile takes its n - 1 arguments from here
+  __shared__ float2 s_l2q[LA];
+  __shared__ float2 s_l2p[kCB];
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
@@ -836,6 +840,10 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
     for (int i = 0; i < kColsBRing; ++i) mbar_init(mbar0 + 8u * i, 1u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (!FP64S) {
+    for (int i = threadIdx.x; i < LA; i += THREADS) s_l2q[i] = sc.l2ff[c + B * i];
+    if (threadIdx.x < kCB) s_l2p[threadIdx.x] = sc.l2ff[col0 + threadIdx.x];
+  }
   __syncthreads();
   const int nplanes = p1 - p0;
   int issued = 0;  // thread 0: planes (indices within the call) whose tile copy is issued
@@ -846,7 +854,8 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
   if (threadIdx.x == 0)
     for (; issued < kColsBRing && issued < nplanes; ++issued) issue(issued);
   // output e = b R1 + r of this thread is line element jt + b TPL + 16 r, image row c + B (that)
-  auto out_row = [&](int e) { return c + B * (jt + (e / R1) * TPL + 16 * (e % R1)); };
+  auto out_line = [&](int e) { return jt + (e / R1) * TPL + 16 * (e % R1); };
+  auto out_row = [&](int e) { return c + B * out_line(e); };
   int P = p0;
   bool failed = false;
   while (P < p1 && !failed) {
@@ -867,7 +876,7 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
           screen_anchor<true, true>(sc, kp, kq, P, img, 1.0f, a, st);
         } else {
           bool valid;
-          const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+          const ff t = n_minus_one_ff(s_l2p[col], s_l2q[out_line(e)], valid);
           st = valid ? cis_cycles_ff(ff_mul({dwI.x, dwI.y}, t)) : make_float2(0.0f, 0.0f);
         }
         s_cstep[e][threadIdx.x] = make_float2(st.x, -st.y);
@@ -929,7 +938,7 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
             screen_anchor<true, false>(sc, kp, kq, P, img, sg, a, st);
           } else {
             bool valid;
-            const ff t = n_minus_one_ff(sc.l2ff[kp], sc.l2ff[kq], valid);
+            const ff t = n_minus_one_ff(s_l2p[col], s_l2q[out_line(e)], valid);
             a = valid ? cis_cycles_ff(ff_mul({wP.x, wP.y}, t)) : make_float2(0.0f, 0.0f);
             a.x *= sg;
             a.y *= sg;

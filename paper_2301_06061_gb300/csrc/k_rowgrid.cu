@@ -359,7 +359,9 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
   __syncthreads();  // the row buffer is reused by the next row
 }
 
-constexpr int kRowBatch = 32;  // rows handed out per counter fetch (one row per CTA step)
+// rows handed out per counter fetch (one row per CTA step); warp 0 scans a batch, one
+// lane per row.  Eight rows keep the end of the kernel's row stream balanced.
+constexpr int kRowBatch = 8;
 
 template <int N, bool FFT, int WT>
 __global__ void __launch_bounds__(RowCfg<N>::THREADS)
@@ -422,7 +424,7 @@ k_grid_rows(const Record *__restrict__ rec, const uint32_t *__restrict__ off, in
       if (base >= total) break;
       if (threadIdx.x < 32) {
         const long long item = base + threadIdx.x;
-        const bool valid = item < total;
+        const bool valid = (int)threadIdx.x < kRowBatch && item < total;
         const bool nonempty = valid && !row_empty(item);
         if (valid) occ[item] = nonempty ? 1 : 0;
         // plain gridding hands the planes to the caller: it also lists the empty rows,
