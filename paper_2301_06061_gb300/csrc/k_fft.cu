@@ -816,10 +816,12 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
   constexpr int NTW = total_tw_count<LA, EPT>();
   __shared__ float2 s_tw1[NTW][TPL];
   __shared__ __align__(8) unsigned long long s_mbar[kColsBRing];
-  // l^2 (float-float) of the tile's LA grid rows c + B m and of its kCB columns, read
-  // once: every screen evaluation of the tile takes its n - 1 arguments from here
+  // l^2 (float-float) and the grid correction 1/Ghat of the tile's LA grid rows c + B m
+  // and of its kCB columns, read once: every screen evaluation of the tile takes its
+  // n - 1 arguments from here, and the flush its correction factors
   __shared__ float2 s_l2q[LA];
   __shared__ float2 s_l2p[kCB];
+  __shared__ float s_corq[LA], s_corp[kCB];
   const int B = n / LA;
   const int col = threadIdx.x % kCB, jt = threadIdx.x / kCB;
   const int c = blockIdx.y;
@@ -843,6 +845,10 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
   if (!FP64S) {
     for (int i = threadIdx.x; i < LA; i += THREADS) s_l2q[i] = sc.l2ff[c + B * i];
     if (threadIdx.x < kCB) s_l2p[threadIdx.x] = sc.l2ff[col0 + threadIdx.x];
+  }
+  if (flags & ACC_CORRECT) {
+    for (int i = threadIdx.x; i < LA; i += THREADS) s_corq[i] = sc.corr[c + B * i];
+    if (threadIdx.x < kCB) s_corp[threadIdx.x] = sc.corr[col0 + threadIdx.x];
   }
   __syncthreads();
   const int nplanes = p1 - p0;
@@ -964,7 +970,7 @@ k_cols_b_tma(const __grid_constant__ CUtensorMap tmap, int p0, int p1, int n_w, 
       const int kq = out_row(e);
       if (CROP && (kq < crop || kq >= crop + n_img || kp < crop || kp >= crop + n_img))
           continue;  // a grid row or column outside the image
-      const float f = (flags & ACC_CORRECT) ? sc.corr[kp] * sc.corr[kq] : 1.0f;
+      const float f = (flags & ACC_CORRECT) ? s_corp[col] * s_corq[out_line(e)] : 1.0f;
       flush_pixel(im, cp, (size_t)(kq - crop) * n_img + (kp - crop), S[e], Cc[e], first_any, last_any, flags, f);
     }
   }

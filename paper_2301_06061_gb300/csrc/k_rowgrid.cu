@@ -130,10 +130,11 @@ __device__ __forceinline__ void cp_async16_rg(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
-// The previous row's transformed values, written out while this row is gridded: four of
-// a thread's outputs per record it grids, the rest when its gridding ends, so that a
-// row's 128 KB leave the SM spread over the next row's gridding instead of in one burst
-// at the end of its transform.
+// The previous row's transformed values, written out while this row is gridded: two
+// groups of four of a thread's outputs while the row's offsets load, then four per
+// record it grids, the rest when its gridding ends, so that a row's 128 KB leave the SM
+// spread over the next row's gridding instead of in one burst at the end of its
+// transform.
 template <int N>
 struct PendingRow {
   static constexpr int EPT = RowCfg<N>::EPT, TPR = RowCfg<N>::TPR, CH = 4, NCH = EPT / CH;
@@ -274,6 +275,10 @@ __device__ __forceinline__ void grid_one_row(float2 *srow, uint32_t *bnd, const 
     for (int i = jt; i <= d_lo + 1; i += TPR) bnd[i] = off[(b0 + q - d_lo + i) * kColBlocks];
     if constexpr (kFixedRows<N>) mb = __ldg(rowbound + b0 + q);
   }
+  // two groups of the previous row's outputs go out while the offsets load (more, or one
+  // more after the first record heads are requested, measured slower)
+  pd.write_one(jt);
+  pd.write_one(jt);
   zero_row<N>(srow, jt);
   __syncthreads();
   // the same decision and quantum in every thread of the row
