@@ -169,6 +169,15 @@ __device__ __forceinline__ float2 twiddle(const Tw &tw, int idx, int dir) {
   return w;
 }
 
+// exp(dir 2 pi i idx / N) evaluated on the spot, for a factor that a kernel needs at once
+// rather than after a table load: with N a power of two and 0 <= idx < N, idx * (2 / N)
+// is exact in FP32, so sincospi sees the exact argument.
+__device__ __forceinline__ float2 twiddle_direct(int idx, float two_over_n, int dir) {
+  float s, c;
+  sincospif((float)idx * two_over_n, &s, &c);
+  return make_float2(c, dir > 0 ? s : -s);
+}
+
 // Butterfly b of this thread has index j = jt + b * TPL (< L/R); its inputs sit at
 // j + r L/R and, after the twiddles w_{NS R}^{(j mod NS) r} and the radix-R DFT, its
 // outputs belong at (j / NS) NS R + (j mod NS) + r NS.

@@ -273,7 +273,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // keeps two CTAs per SM with the deeper ring.  A warp covers 32 columns at one line
 // position: shared-memory accesses are conflict-free without padding and twiddles are
 // warp-uniform.  The factors w_N^{a c} of a tile come from a shared table filled with the
-// tile (three in rotation).
+// tile (three in rotation), each factor evaluated by sincospi.
 template <int LB, int DIR, bool TW_FIRST>
 __global__ void __launch_bounds__(LB / 16 * 32, 512 / (LB / 16 * 32))
 k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict__ occ, int nplanes) {
@@ -315,9 +315,12 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
         reinterpret_cast<float4 *>(buf)[(i * CB + 2 * part) / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   };
+  // evaluated, not loaded: a table load here stalled the filling warps for an L2 round
+  // trip on every tile, and the CTA's other warps then waited for them at the next barrier
+  const float two_over_n = 2.0f / (float)n;
   auto fill_tw = [&](int t, float2 *dst) {
     const int a = (t >> lg_bands) & (A - 1);
-    if (threadIdx.x < LB) dst[threadIdx.x] = twiddle(tw, (a * (int)threadIdx.x) & (n - 1), DIR);
+    if (threadIdx.x < LB) dst[threadIdx.x] = twiddle_direct((a * (int)threadIdx.x) & (n - 1), two_over_n, DIR);
   };
   int t = blockIdx.x;
   bool f0[PPT], f1[PPT];
