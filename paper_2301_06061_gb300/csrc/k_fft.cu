@@ -292,15 +292,17 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
   float2 twr[total_tw_count<LB, EPT>()];
   all_twiddles<LB, EPT, TPL, DIR>(twr, jt, tw, A);
   const size_t rstride = (size_t)A * n;  // line element i -> row a + A*i
-  auto load_flags = [&](int t, bool (&f)[PPT]) {
+  // the occupancy bytes of a tile's rows, loaded a tile ahead and kept raw until issue()
+  // tests them: turning them into booleans at once made every warp wait for the loads
+  auto load_flags = [&](int t, uint32_t (&f)[PPT]) {
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
       const int i = (threadIdx.x + k * THREADS) / (CB / 2);
-      f[k] = t >= total || !occ || occ[(size_t)z * n + a + A * i];
+      f[k] = (t >= total || !occ) ? 1u : (uint32_t)occ[(size_t)z * n + a + A * i];
     }
   };
-  auto issue = [&](int t, float2 *buf, const bool (&f)[PPT]) {
+  auto issue = [&](int t, float2 *buf, const uint32_t (&f)[PPT]) {
     const int band = t & ((1 << lg_bands) - 1);
     const int a = (t >> lg_bands) & (A - 1), z = t >> (lg_bands + lg_A);
     const float2 *src = planes + (size_t)z * n * n + (size_t)a * n + band * CB;
@@ -323,7 +325,7 @@ k_cols_a16(float2 *__restrict__ planes, Tw tw, int n, const uint8_t *__restrict_
     if (threadIdx.x < LB) dst[threadIdx.x] = twiddle_direct((a * (int)threadIdx.x) & (n - 1), two_over_n, DIR);
   };
   int t = blockIdx.x;
-  bool f0[PPT], f1[PPT];
+  uint32_t f0[PPT], f1[PPT];
   const int G = gridDim.x;
   // tiles it and it + 1 in flight before the loop; tile it + 2 is issued after the first
   // barrier of tile it, into the slot of tile it - 1
